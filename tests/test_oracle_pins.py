@@ -1,0 +1,355 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and the mathematics.
+
+Each test checks the oracle against something other than itself: a brute-force
+or library solver of the same optimisation problem, a closed form (Riccati,
+Sherman-Morrison), an invariant of Sec. II-A (Z_AB Psi = I, Phi = Psi at
+convergence, support inside L_d) or the Lemma of Sec. III-B.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.optimize
+
+from oracle import dlmpc_oracle as O
+from paper_2103_14990_gb300 import instances as I
+
+
+# --------------------------------------------------------------------------
+# Phi-step: one row of the box-QP (Alg. 2 Phi-comp)
+# --------------------------------------------------------------------------
+
+def _row_obj(phi, v, xh, q, rho):
+    z = phi @ xh
+    return q * z * z + 0.5 * rho * np.sum((phi - v) ** 2)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_phi_row_matches_slsqp(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 7))
+    v = rng.normal(size=n)
+    xh = rng.normal(size=n)
+    q = float(rng.uniform(0.2, 3.0))
+    rho = float(rng.uniform(0.3, 3.0))
+    lo, hi = sorted(rng.normal(size=2) * 0.5)
+    got = O.phi_step_row(v, xh, q, rho, lo, hi)
+    cons = [{"type": "ineq", "fun": lambda p: p @ xh - lo, "jac": lambda p: xh},
+            {"type": "ineq", "fun": lambda p: hi - p @ xh, "jac": lambda p: -xh}]
+    ref = scipy.optimize.minimize(
+        _row_obj, v, args=(v, xh, q, rho),
+        jac=lambda p, *a: 2 * q * (p @ xh) * xh + rho * (p - v),
+        constraints=cons, method="SLSQP", options={"ftol": 1e-15, "maxiter": 500})
+    assert ref.success
+    assert np.allclose(got, ref.x, atol=1e-6)
+    assert _row_obj(got, v, xh, q, rho) <= _row_obj(ref.x, v, xh, q, rho) + 1e-10
+    # KKT: rho (phi - v) + (2 q z + mu) xh = 0, mu >= 0 at hi, <= 0 at lo, 0 inside
+    z = got @ xh
+    g = rho * (got - v) + 2 * q * z * xh
+    mu = -(g @ xh) / (xh @ xh)
+    assert np.allclose(g + mu * xh, 0, atol=1e-10)
+    if lo + 1e-9 < z < hi - 1e-9:
+        assert abs(mu) < 1e-9
+    elif abs(z - hi) <= 1e-9:
+        assert mu >= -1e-9
+    else:
+        assert abs(z - lo) <= 1e-9 and mu <= 1e-9
+
+
+def test_phi_row_special_cases():
+    rng = np.random.default_rng(7)
+    v, xh = rng.normal(size=5), rng.normal(size=5)
+    # no bounds: (rho I + 2 q xh xh^T) phi = rho v (Sherman-Morrison)
+    q, rho = 1.3, 0.7
+    got = O.phi_step_row(v, xh, q, rho, -np.inf, np.inf)
+    ref = np.linalg.solve(rho * np.eye(5) + 2 * q * np.outer(xh, xh), rho * v)
+    assert np.allclose(got, ref, atol=1e-12)
+    # q = 0 and w inside the box: phi = v
+    assert np.allclose(O.phi_step_row(v, xh, 0.0, rho, -1e9, 1e9), v)
+    # xh = 0: phi = v
+    assert np.allclose(O.phi_step_row(v, np.zeros(5), q, rho, -1.0, 1.0), v)
+    # active bound: the row's output is exactly the bound
+    big = v + 10 * xh / (xh @ xh)
+    out = O.phi_step_row(big, xh, 0.01, rho, -0.5, 0.5)
+    assert abs(out @ xh - 0.5) < 1e-12
+
+
+def test_vectorised_phi_step_agrees_with_rows():
+    p = I.make_instance(6, 4, 1, seed=3, boxes=True, x0_dist="uniform", x_bound=0.3, u_bound=0.2)
+    lay = O.Layout(p)
+    rng = np.random.default_rng(1)
+    Psi, Lam = rng.normal(size=lay.nnz), rng.normal(size=lay.nnz)
+    Phi, z = O.phi_step(lay, Psi, Lam, p.x0, p.rho)
+    xf = p.x0.reshape(-1)
+    for g in range(lay.n_rows):
+        ent = np.nonzero(lay.rows == g)[0]
+        ref = O.phi_step_row((Psi - Lam)[ent], xf[lay.cols[ent]], lay.qw[g], p.rho, lay.lo[g], lay.hi[g])
+        assert np.allclose(Phi[ent], ref, atol=1e-12)
+        assert abs(z[g] - ref @ xf[lay.cols[ent]]) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Psi-step: projection onto the achievability constraint (Alg. 2 Psi-comp)
+# --------------------------------------------------------------------------
+
+def _small_problems():
+    return [I.chain10(), I.make_instance(9, 4, 1, graph="grid", seed=5),
+            I.make_instance(7, 5, 2, graph="chain", seed=2)]
+
+
+@pytest.mark.parametrize("k", range(3))
+def test_projector_properties(k):
+    p = _small_problems()[k]
+    rng = np.random.default_rng(k)
+    for j in range(p.n_sub):
+        b = O.column_block(p, j)
+        D = b.P.shape[0]
+        assert b.feas < 1e-12
+        assert np.allclose(b.P, b.P.T, atol=1e-10)
+        assert np.allclose(b.P @ b.P, b.P, atol=1e-10)
+        assert np.allclose(b.Z @ b.P, 0, atol=1e-10)
+        Nul = scipy.linalg.null_space(b.Z)
+        assert Nul.shape[1] == D - b.rank
+        assert np.allclose(Nul @ Nul.T, b.P, atol=1e-10)
+        for a in range(p.nx):
+            ls = np.linalg.lstsq(b.Z, b.rhs[a], rcond=None)[0]
+            assert np.allclose(ls, b.q[a], atol=1e-10)
+            v = rng.normal(size=D)
+            psi = b.P @ v + b.q[a]
+            assert np.allclose(b.Z @ psi, b.rhs[a], atol=1e-11)
+            assert np.allclose(Nul.T @ (psi - v), 0, atol=1e-10)
+
+
+def test_constraint_block_counts():
+    """Rows kept / rank / nullity of Z_j, derived by hand for the chain plant.
+
+    Interior chain subsystem, d hops: the patch has 2d+1 members and the ring
+    adds 2 more.  Rows kept = nx*T per patch member, plus per ring-only member
+    the T-1 second-state rows (its first-state rows and its slot-0 rows have
+    no patch variable).  Each ring-only member makes its slot-1 row redundant
+    with the slot-0 rows of the patch, so rank = rows - 2.  Ends lose one ring
+    member and one redundancy.
+    """
+    for (T, d) in [(5, 1), (10, 3), (15, 3)]:
+        p = I.make_instance(4 * d + 6, T, d, seed=0)
+        rs = 3 * T - 1
+        mid = O.column_block(p, 2 * d + 3)
+        npatch = 2 * d + 1
+        rows = 2 * T * npatch + 2 * (T - 1)
+        assert mid.Z.shape == (rows, rs * npatch)
+        assert mid.rank == rows - 2
+        end = O.column_block(p, 0)
+        rows_e = 2 * T * (d + 1) + (T - 1)
+        assert end.Z.shape == (rows_e, rs * (d + 1))
+        assert end.rank == rows_e - 1
+
+
+# --------------------------------------------------------------------------
+# Lemma of Sec. III-B: D_row and D_col bounds
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("graph,n,T,d", [("chain", 20, 5, 1), ("chain", 30, 10, 3),
+                                         ("grid", 49, 10, 2), ("grid", 36, 6, 3),
+                                         ("grid", 27, 5, 1)])
+def test_lemma_bounds(graph, n, T, d):
+    p = I.make_instance(n, T, d, graph=graph, seed=1)
+    l = max(int(p.adj_ptr[i + 1] - p.adj_ptr[i]) for i in range(n))
+    s = max(p.nx, p.nu)
+    brow, bcol = O.lemma_bounds(s, l, d, T)
+    for j in range(n):
+        m = len(O.patch_members(p, j))
+        assert p.nx * m <= brow                 # D_row: entries of one Phi row
+        assert p.r_sub * m <= bcol              # D_col: entries of one Psi column
+
+
+# --------------------------------------------------------------------------
+# Whole ADMM against the centralised problem
+# --------------------------------------------------------------------------
+
+def _support_mask(p):
+    lay = O.Layout(p)
+    M = np.zeros((lay.n_rows, p.n_sub * p.nx), bool)
+    M[lay.rows, lay.cols] = True
+    return lay, M
+
+
+def _centralised_affine(p, x0):
+    """y = y0 + G theta over every Phi in L_d with Z_AB Phi = I (all rows of Z_AB)."""
+    Z = O.global_Z_AB(p)
+    lay, M = _support_mask(p)
+    ncol = p.n_sub * p.nx
+    y0 = np.zeros(lay.n_rows)
+    blocks = []
+    for c in range(ncol):
+        idx = np.nonzero(M[:, c])[0]
+        Zc = Z[:, idx]
+        e = np.zeros(Z.shape[0]); e[c] = 1.0
+        part = np.linalg.lstsq(Zc, e, rcond=None)[0]
+        assert np.allclose(Zc @ part, e, atol=1e-10)
+        Nc = scipy.linalg.null_space(Zc)
+        col = np.zeros(lay.n_rows); col[idx] = part
+        y0 += x0.reshape(-1)[c] * col
+        Gc = np.zeros((lay.n_rows, Nc.shape[1])); Gc[idx] = Nc
+        blocks.append(x0.reshape(-1)[c] * Gc)
+    return lay, y0, np.hstack(blocks)
+
+
+def test_admm_matches_centralised_least_squares():
+    p = I.make_instance(5, 4, 1, seed=11, boxes=False, x0_dist="normal")
+    lay, y0, G = _centralised_affine(p, p.x0)
+    W = np.sqrt(lay.qw)
+    theta = np.linalg.lstsq(W[:, None] * G, -W * y0, rcond=None)[0]
+    y_ref = y0 + G @ theta
+    o = O.Oracle(p)
+    res = O.admm(o.lay, o.blocks, p.x0, max_iter=20000, eps_p=1e-11, eps_d=1e-11)
+    assert res.status == O.STATUS_CONVERGED
+    y = o.lay.trajectory(res.Phi, p.x0)
+    assert np.allclose(y, y_ref, atol=1e-8)
+
+
+def test_admm_matches_centralised_boxed_qp():
+    """Boxed case.  The trajectory lives in y0 + range(G); with an orthonormal
+    basis Bm of range(G) the centralised QP is strictly convex in phi.  Its
+    dual (lambda >= 0) is solved by L-BFGS-B; the active set it exposes is then
+    solved exactly as an equality-constrained KKT system, whose multipliers
+    must carry the right signs.  The instance is feasible and its unconstrained
+    optimum violates the box, so the box is exercised."""
+    p = I.make_instance(4, 4, 1, seed=3, boxes=True, x0_dist="uniform", x_bound=1.0, u_bound=0.1)
+    p.x0 = 0.9 * p.x0
+    lay, y0, G = _centralised_affine(p, p.x0)
+    U, S, _ = np.linalg.svd(G, full_matrices=False)
+    Bm = U[:, S > 1e-10 * S[0]]
+    bnd = np.isfinite(lay.lo)
+    assert np.array_equal(bnd, np.isfinite(lay.hi))
+    C = np.vstack([Bm[bnd], -Bm[bnd]])                       # C phi <= b
+    b = np.concatenate([lay.hi[bnd] - y0[bnd], y0[bnd] - lay.lo[bnd]])
+    W = lay.qw
+    H = 2 * Bm.T @ (W[:, None] * Bm)
+    f = 2 * Bm.T @ (W * y0)
+    Hinv = np.linalg.inv(H)
+    phi_unc = -Hinv @ f
+    assert np.max(C @ phi_unc - b) > 1e-3, "unconstrained optimum must violate the box"
+    M = C @ Hinv @ C.T
+    g0 = C @ Hinv @ f + b
+    dual = scipy.optimize.minimize(lambda l: 0.5 * l @ M @ l + g0 @ l, np.zeros(len(b)),
+                                   jac=lambda l: M @ l + g0, method="L-BFGS-B",
+                                   bounds=[(0, None)] * len(b),
+                                   options={"ftol": 1e-16, "gtol": 1e-13, "maxiter": 20000})
+    act = dual.x > 1e-7
+    assert act.sum() >= 1
+    Ca, ba = C[act], b[act]
+    nC = Ca.shape[0]
+    K = np.block([[H, Ca.T], [Ca, np.zeros((nC, nC))]])
+    sol = np.linalg.solve(K, np.concatenate([-f, ba]))
+    phi, lam = sol[:H.shape[0]], sol[H.shape[0]:]
+    assert np.all(lam >= -1e-10)                              # dual feasibility
+    assert np.all(C @ phi <= b + 1e-10)                       # primal feasibility
+    y_ref = y0 + Bm @ phi
+    o = O.Oracle(p)
+    res = O.admm(o.lay, o.blocks, p.x0, max_iter=50000, eps_p=1e-10, eps_d=1e-10)
+    assert res.status == O.STATUS_CONVERGED
+    y = o.lay.trajectory(res.Phi, p.x0)
+    assert np.allclose(y, y_ref, atol=1e-6)
+    assert abs(np.sum(W * y * y) - np.sum(W * y_ref * y_ref)) < 1e-8
+
+
+def _riccati_u0(A, B, Q, R, T, x0):
+    P = Q.copy()                           # P_{T-1} = Q (last state slot)
+    for _ in range(T - 2):                 # P_{T-2} .. P_1
+        S = R + B.T @ P @ B
+        P = Q + A.T @ P @ A - A.T @ P @ B @ np.linalg.solve(S, B.T @ P @ A)
+    return -np.linalg.solve(R + B.T @ P @ B, B.T @ P @ A @ x0)
+
+
+@pytest.mark.parametrize("n,T", [(3, 4), (4, 5)])
+def test_admm_matches_riccati_without_locality(n, T):
+    """d >= N-1 removes locality; with no boxes u(0) is the finite-horizon LQR
+    gain applied to x0.  Non-identity diagonal Q, R (with Q = R = I the
+    min-norm projection alone already gives the LQR map)."""
+    p = I.make_instance(n, T, n - 1, seed=21, boxes=False, x0_dist="normal")
+    rng = np.random.default_rng(5)
+    p.q = rng.uniform(0.3, 3.0, p.q.shape)
+    p.r = rng.uniform(0.3, 3.0, p.r.shape)
+    A, B = p.dense_A(), p.dense_B()
+    u_ref = _riccati_u0(A, B, np.diag(p.q.reshape(-1)), np.diag(p.r.reshape(-1)), T, p.x0.reshape(-1))
+    o = O.Oracle(p)
+    res = O.admm(o.lay, o.blocks, p.x0, max_iter=50000, eps_p=1e-11, eps_d=1e-11)
+    assert res.status == O.STATUS_CONVERGED
+    assert np.allclose(o.control(res).reshape(-1), u_ref, atol=1e-8)
+
+
+@pytest.mark.parametrize("k", range(3))
+def test_invariants_after_admm(k):
+    p = _small_problems()[k]
+    o = O.Oracle(p)
+    res = O.admm(o.lay, o.blocks, p.x0, max_iter=20000, eps_p=1e-9, eps_d=1e-9)
+    assert res.status == O.STATUS_CONVERGED
+    Z = O.global_Z_AB(p)
+    Psi = o.lay.to_dense(res.Psi)
+    rhs = np.zeros((Z.shape[0], p.n_sub * p.nx)); rhs[:p.n_sub * p.nx] = np.eye(p.n_sub * p.nx)
+    assert np.max(np.abs(Z @ Psi - rhs)) < 1e-10          # Z_AB Psi = I
+    assert np.max(np.abs(res.Phi - res.Psi)) < 1e-8      # Phi = Psi at convergence
+    # support inside L_d: every stored entry links subsystems at most d hops apart
+    near = {i: O.hop_distances(p, i, p.d) for i in range(p.n_sub)}
+    assert all(int(c) in near[int(r)] for r, c in zip(o.lay.row_sub, o.lay.col_sub))
+    y = o.lay.trajectory(res.Phi, p.x0)
+    assert np.all(y <= o.lay.hi + 1e-8) and np.all(y >= o.lay.lo - 1e-8)
+
+
+def test_dual_update_and_closed_loop_dynamics():
+    p = I.chain10()
+    o = O.Oracle(p)
+    r1 = O.admm(o.lay, o.blocks, p.x0, fixed_iters=1)
+    r2 = O.admm(o.lay, o.blocks, p.x0, fixed_iters=2)
+    Phi2, _ = O.phi_step(o.lay, r1.Psi, r1.Lam, p.x0, p.rho)
+    assert np.allclose(r2.Lam, r1.Lam + Phi2 - r2.Psi, atol=1e-13)  # Lambda-comp
+    xs, us, its, _ = o.run_mpc(2, warm="cold")
+    A, B = p.dense_A(), p.dense_B()
+    assert np.allclose(xs[1].reshape(-1), A @ p.x0.reshape(-1) + B @ us[0].reshape(-1))
+
+
+# --------------------------------------------------------------------------
+# Planted mistakes: each one must be caught by a pin above
+# --------------------------------------------------------------------------
+
+def test_planted_dropped_cost_is_caught(monkeypatch):
+    p = I.make_instance(3, 4, 2, seed=21, boxes=False, x0_dist="normal")
+    orig = O.phi_step
+    def bad(lay, Psi, Lam, x0, rho):
+        saved = lay.qw.copy(); lay.qw[:] = 0.0
+        try:
+            return orig(lay, Psi, Lam, x0, rho)
+        finally:
+            lay.qw[:] = saved
+    monkeypatch.setattr(O, "phi_step", bad)
+    with pytest.raises(AssertionError):
+        test_admm_matches_riccati_without_locality(3, 4)
+
+
+def test_planted_missing_ring_rows_is_caught(monkeypatch):
+    orig = O.ring_members
+    monkeypatch.setattr(O, "ring_members", lambda prob, j: O.patch_members(prob, j))
+    with pytest.raises(AssertionError):
+        test_invariants_after_admm(0)
+    monkeypatch.setattr(O, "ring_members", orig)
+
+
+def test_planted_transposed_coupling_is_caught(monkeypatch):
+    orig = O.z_row_coeffs
+    def bad(prob, i, t, a):
+        out = orig(prob, i, t, a)
+        return [((k, r), (-val if (k != i and val != 0) else val)) for (k, r), val in out]
+    monkeypatch.setattr(O, "z_row_coeffs", bad)
+    with pytest.raises(AssertionError):
+        test_dual_update_and_closed_loop_dynamics_consistency()
+
+
+def test_dual_update_and_closed_loop_dynamics_consistency():
+    """Z_AB rows must reproduce the plant: the slot-1 row of Psi x0 equals A x0 + B u_0."""
+    p = I.make_instance(6, 4, 5, seed=8, boxes=False, x0_dist="normal")
+    o = O.Oracle(p)
+    res = O.admm(o.lay, o.blocks, p.x0, max_iter=20000, eps_p=1e-10, eps_d=1e-10)
+    y = o.lay.trajectory(res.Psi, p.x0)
+    Nx = p.n_sub * p.nx
+    x1 = y[Nx:2 * Nx]
+    u0 = y[p.T * Nx:p.T * Nx + p.n_sub]
+    assert np.allclose(x1, p.dense_A() @ p.x0.reshape(-1) + p.dense_B() @ u0, atol=1e-8)
