@@ -1,0 +1,175 @@
+/*
+ * dlmpc.h - C ABI of the GB300 DLMPC solver.
+ *
+ * Distributed and localized MPC (Sec. II-A): at every MPC step (Alg. 1) an ADMM
+ * over the system-level parameterisation Phi runs until convergence (Alg. 2):
+ *   Phi-comp     row-wise box-QP on Phi x(tau)          (Alg. 2, Phi-comp)
+ *   Psi-comp     column-wise projection onto Z_AB Psi = I within the d-hop patch
+ *   Lambda-comp  Lambda <- Lambda + Phi - Psi
+ *   Conv         per-subsystem primal/dual residuals, global AND
+ * and the first input slot of Phi x(tau) is applied: x(tau+1) = A x + B u.
+ *
+ * Conventions shared by every entry point:
+ *  - One context holds n_inst >= 1 independent instances; all share nx and nu,
+ *    T and d may differ.  Subsystems of all instances are concatenated in
+ *    instance order ("global subsystem index").
+ *  - Phi has T state slots (t = 0..T-1) and T-1 input slots per subsystem:
+ *    r_sub = nx*T + nu*(T-1) rows per subsystem (Sec. II-A, shape of Phi).
+ *  - Locality: Phi(row of i, column of j) may be nonzero iff the hop distance
+ *    of i and j on the coupling graph is <= d.  Patch(j) lists those i in
+ *    ascending order.
+ *  - Column-owned state layout (get/set_state): for every global subsystem j,
+ *    for every own column c < nx, for every member m of Patch(j) (ascending),
+ *    for every local row r < r_sub: one float.  Local rows are ordered state
+ *    slot-major (t*nx + a for t < T), then inputs (nx*T + t*nu + b).
+ *  - Pointers named *_dev are device pointers that must be valid on the
+ *    context's stream; every other pointer is host memory.  The caller keeps
+ *    ownership of everything it passes; the library copies setup inputs and
+ *    owns all its workspaces.
+ *  - Return codes: 0 = OK, > 0 soft status, < 0 error.  No C++ exception or
+ *    abort crosses this boundary; dlmpc_last_error() explains the last error.
+ *  - Calls are asynchronous on the context's stream unless they return host
+ *    statistics, which synchronise on that stream.
+ */
+#ifndef DLMPC_H
+#define DLMPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DLMPC_OK 0
+#define DLMPC_MAX_ITER 1                 /* ADMM stopped at max_iter; results still written */
+#define DLMPC_ERR_ARG (-1)               /* invalid argument or call order */
+#define DLMPC_ERR_INFEASIBLE_LOCALITY (-2) /* some Z_j psi = e_c has no solution */
+#define DLMPC_ERR_NONFINITE (-3)         /* NaN/Inf residual during ADMM */
+#define DLMPC_ERR_TIMEOUT (-4)           /* a device-side wait gave up (bounded spin) */
+#define DLMPC_ERR_CUDA (-5)              /* a CUDA runtime call failed */
+#define DLMPC_ERR_NOMEM (-6)             /* device allocation failed */
+
+#define DLMPC_WARM_COLD 0      /* Psi = Lambda = 0 */
+#define DLMPC_WARM_PREVIOUS 1  /* continue from the state left by the previous step/set_state */
+#define DLMPC_WARM_LEARNED 2   /* learned initial Phi rows and Lambda, then a Psi-step first */
+
+typedef struct dlmpc_ctx dlmpc_ctx;
+
+/* One DLMPC instance: Eq. (MPC) of Sec. II-A with Q_t = Q, R_t = R for all t.
+ * The coupling graph G_(A,B) is undirected, CSR, without self loops; column
+ * indices ascending within each row.  Bounds apply to states of slots 1..T-1
+ * and to all inputs; NULL means unbounded. */
+typedef struct {
+  int32_t n_sub, nx, nu, T, d;
+  const int32_t *adj_ptr;   /* [n_sub+1] */
+  const int32_t *adj_idx;   /* [adj_ptr[n_sub]] */
+  const double *A_diag;     /* [n_sub][nx][nx] row-major A_ii */
+  const double *A_off;      /* [nnz][nx][nx]   A_{i,adj_idx[e]} for CSR entry e of row i */
+  const double *B;          /* [n_sub][nx][nu] B_ii (B block diagonal) */
+  const double *q;          /* [n_sub][nx] diagonal of Q_i (> 0) */
+  const double *r;          /* [n_sub][nu] diagonal of R_i (> 0) */
+  const double *x_lo, *x_hi;/* [n_sub][nx] or NULL */
+  const double *u_lo, *u_hi;/* [n_sub][nu] or NULL; 0 must lie in [u_lo, u_hi] */
+  double rho;               /* ADMM penalty (> 0) */
+  double eps_p, eps_d;      /* Conv thresholds on the per-subsystem residuals */
+  int32_t max_iter;         /* ADMM iteration cap (>= 1) */
+} dlmpc_problem;
+
+/* Per-instance result of one MPC step. */
+typedef struct {
+  int32_t iters;            /* ADMM iterations run */
+  int32_t status;           /* DLMPC_OK (converged) or DLMPC_MAX_ITER */
+  float r_max;              /* max_j ||Phi - Psi||_F over j's columns, last iteration */
+  float s_max;              /* max_j rho ||Psi^{k+1} - Psi^k||_F over j's columns */
+} dlmpc_stats;
+
+/* Sizes of a context (host struct filled by dlmpc_get_info). */
+typedef struct {
+  int32_t n_inst, n_sub_total, nx, nu;
+  int32_t n_items;          /* column patches = n_sub_total */
+  int32_t max_dcol, max_nullity;
+  int64_t state_floats;     /* floats of one column-owned matrix (Phi, Psi or Lambda) */
+  int64_t operator_bytes;   /* bytes of all null-space bases N_j (FP32, padded) */
+  int64_t offset_bytes;     /* bytes of all min-norm offsets q_c (FP32, padded) */
+  int64_t exchange_floats;  /* floats of one row-partial-sum exchange buffer */
+  int32_t grid_ctas, threads_per_cta, smem_bytes; /* launch of the ADMM sweep kernel */
+} dlmpc_info;
+
+/* Option keys for dlmpc_set_option. */
+#define DLMPC_OPT_FIXED_ITERS 1   /* > 0: run exactly this many iterations, Conv only reported */
+#define DLMPC_OPT_MAX_ITER 2      /* overrides every instance's max_iter */
+#define DLMPC_OPT_TIMEOUT_MS 3    /* bound of every device-side wait (default 2000) */
+#define DLMPC_OPT_EXPORT_PHI 4    /* != 0: keep the last Phi for dlmpc_get_state */
+#define DLMPC_OPT_CTAS_PER_SM 5   /* ADMM sweep CTAs per SM (0 = occupancy maximum) */
+#define DLMPC_OPT_SMEM_BYTES 6    /* dynamic shared memory of the sweep kernel (0 = auto) */
+#define DLMPC_OPT_TIMING 7        /* != 0: record CUDA events around every step (dlmpc_get_timing) */
+
+/* Builds the locality structure (hop-distance BFS, Patch(j), rows of Z_AB that
+ * touch each patch) for n_inst instances, copies all inputs to the device and
+ * allocates workspaces.  Sec. III-B "Setup".  probs: host array [n_inst].
+ * stream: a cudaStream_t (NULL = legacy default stream).  On success *out
+ * receives a context to be released with dlmpc_destroy. */
+int dlmpc_setup(const dlmpc_problem *probs, int32_t n_inst, void *stream, dlmpc_ctx **out);
+
+/* One-time precomputation (Alg. 1, first line; Sec. IV-C "Precomputation"):
+ * for every column patch j, an FP64 pivoted Householder QR of the restricted
+ * constraint matrix gives an orthonormal null-space basis N_j and the min-norm
+ * offsets q_c = Z_j^+ e_c (stored FP32).  Returns DLMPC_ERR_INFEASIBLE_LOCALITY
+ * if max_c ||Z_j q_c - e_c|| exceeds 1e-9 for some j. Synchronous. */
+int dlmpc_precompute(dlmpc_ctx *ctx);
+
+/* One MPC step for every instance (Alg. 1 body): per-step precompute from
+ * x(tau), ADMM to convergence (Alg. 2), u(tau) = slot-0 inputs of Phi x(tau),
+ * x(tau+1) = A x(tau) + B u(tau).
+ * x_dev: [n_sub_total][nx] float; u_dev: [n_sub_total][nu] float (written);
+ * x_next_dev: [n_sub_total][nx] float or NULL.  warm: DLMPC_WARM_*.
+ * stats: host [n_inst] or NULL (NULL keeps the call asynchronous).
+ * Returns the worst status over instances (DLMPC_MAX_ITER if any hit the cap)
+ * or an error. */
+int dlmpc_step(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *x_next_dev,
+               int32_t warm, dlmpc_stats *stats);
+
+/* Same as dlmpc_step with one device buffer per instance: x_dev[b], u_dev[b],
+ * x_next_dev[b] (host arrays of n_inst device pointers; x_next_dev may be NULL). */
+int dlmpc_solve_batch(dlmpc_ctx *ctx, const float *const *x_dev, float *const *u_dev,
+                      float *const *x_next_dev, int32_t warm, dlmpc_stats *stats);
+
+/* Same as dlmpc_step with HOST buffers: copies x to the device, runs the step,
+ * copies u (and x_next if non-NULL) back, then synchronises. */
+int dlmpc_step_host(dlmpc_ctx *ctx, const float *x, float *u, float *x_next,
+                    int32_t warm, dlmpc_stats *stats);
+
+int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value);
+int dlmpc_get_info(dlmpc_ctx *ctx, dlmpc_info *info);
+
+/* Copies the state (device pointers, column-owned layout, info.state_floats
+ * floats each; any may be NULL).  phi needs DLMPC_OPT_EXPORT_PHI. */
+int dlmpc_get_state(dlmpc_ctx *ctx, float *phi_dev, float *psi_dev, float *lam_dev);
+/* Replaces Psi and Lambda (device pointers, same layout); used by
+ * DLMPC_WARM_PREVIOUS on the next step. */
+int dlmpc_set_state(dlmpc_ctx *ctx, const float *psi_dev, const float *lam_dev);
+
+/* Host copy of Patch(j) of global subsystem j (members as global indices);
+ * returns |Patch(j)| or an error.  cap = capacity of members. */
+int dlmpc_get_patch(dlmpc_ctx *ctx, int32_t j, int32_t *members, int32_t cap);
+
+/* Host copy of the precomputed operator of column patch j in the FULL
+ * column-owned variable order (D_col = r_sub*|Patch(j)| rows): N (D_col x k,
+ * row-major, slot-0 state rows zero) and q (nx x D_col).  Returns k. */
+int dlmpc_get_operator(dlmpc_ctx *ctx, int32_t j, double *N, int32_t n_cap,
+                       double *q, int32_t q_cap);
+
+/* GPU time of the last step, from CUDA events recorded on the context's
+ * stream (needs DLMPC_OPT_TIMING): ms[0] = the ADMM sweep kernel alone,
+ * ms[1] = the whole step (first memset to the end of the statistics copy).
+ * Waits for the step to finish. */
+int dlmpc_get_timing(dlmpc_ctx *ctx, float *ms);
+
+const char *dlmpc_last_error(dlmpc_ctx *ctx);
+void dlmpc_destroy(dlmpc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DLMPC_H */

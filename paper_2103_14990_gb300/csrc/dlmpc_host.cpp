@@ -1,0 +1,943 @@
+// Host side of the DLMPC solver: locality structure (Sec. II-A, d-hop
+// patches), the reduced per-patch constraint systems, work assignment and the
+// C ABI declared in include/dlmpc.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <numeric>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "dlmpc_internal.h"
+#include "../../include/dlmpc.h"
+
+namespace dlmpc {
+cudaError_t launch_factor(const FactorParams &p, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_repack(const Item *scratch_items, const Item *items, int n_items, const float *src, float *dst,
+                          cudaStream_t s);
+const void *admm_kernel_ptr(int nx);
+int sweep_threads();
+size_t sweep_smem_bytes(int nx, int smem_n_floats, int max_dcol, int max_kpad);
+cudaError_t launch_admm(int nx, const Params &P, int max_dcol, int max_kpad, int grid, size_t smem,
+                        cudaStream_t s);
+cudaError_t launch_stats(const int32_t *inst_item_ptr, int n_inst, const float *item_r, const float *item_s,
+                         const int32_t *inst_iters, const int32_t *err, int fixed, const float *epsp,
+                         const float *epsd, dlmpc_stats *out, cudaStream_t s);
+cudaError_t launch_gather(const float *const *src, const int32_t *off, int n_inst, int width, float *dst,
+                          cudaStream_t s);
+cudaError_t launch_scatter(const float *src, const int32_t *off, int n_inst, int width, float *const *dst,
+                           cudaStream_t s);
+}  // namespace dlmpc
+
+using namespace dlmpc;
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+template <class T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  cudaError_t alloc(size_t count) {
+    release();
+    n = count;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void **>(&p), count * sizeof(T));
+  }
+};
+
+struct Instance {
+  int n_sub = 0, T = 0, d = 0, sub_off = 0, item_off = 0;
+  std::vector<int32_t> adj_ptr, adj_idx;
+  std::vector<double> A_diag, A_off, B, q, r, x_lo, x_hi, u_lo, u_hi;
+  bool has_x = false, has_u = false;
+  double rho = 1, eps_p = 1e-4, eps_d = 1e-4;
+  int max_iter = 1000;
+  std::vector<std::vector<int32_t>> patch;  // local ids, ascending
+  std::vector<std::vector<int32_t>> ring;
+};
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct dlmpc_ctx {
+  cudaStream_t stream = nullptr;
+  int nx = 0, nu = 0, n_inst = 0, n_sub = 0;
+  std::vector<Instance> inst;
+  std::vector<Item> items;
+  std::vector<int32_t> members, rev_slot, np_of;
+  std::vector<int64_t> g_off;
+  int64_t g_floats = 0, state_floats = 0;
+  // reduced constraints
+  std::vector<int64_t> zrow_ptr;
+  std::vector<int32_t> zcol;
+  std::vector<double> zval, rhs;
+  std::vector<int64_t> rhs_off;
+  std::vector<int32_t> kub;
+  bool precomputed = false;
+  int max_dcol = 0, max_kpad = 1;
+  int64_t n_floats = 0, q_floats = 0;
+  // launch
+  int grid = 0, smem_n_floats = 0;
+  size_t smem = 0;
+  std::vector<int32_t> cta_ptr, cta_items;
+  // options
+  int fixed_iters = 0, max_iter_override = 0, export_phi = 0, ctas_per_sm = 0, smem_opt = 0;
+  double timeout_ms = 2000.0;
+  std::string err;
+  // device
+  DevBuf<Item> d_items;
+  DevBuf<int32_t> d_members, d_rev, d_np, d_cta_ptr, d_cta_items, d_adj_ptr, d_adj_idx, d_inst_iters, d_err,
+      d_inst_item_ptr, d_sub_off;
+  DevBuf<int64_t> d_goff;
+  DevBuf<float> d_N, d_q, d_psi, d_lam, d_phi, d_G0, d_G1, d_S, d_qw, d_rw, d_xlo, d_xhi, d_ulo, d_uhi, d_rho,
+      d_epsp, d_epsd, d_item_r, d_item_s, d_x, d_u, d_xn;
+  DevBuf<double> d_Adiag, d_Aoff, d_B;
+  DevBuf<unsigned> d_bar, d_notconv;
+  DevBuf<dlmpc_stats> d_stats;
+  DevBuf<const float *> d_ptr_in;
+  DevBuf<float *> d_ptr_out, d_ptr_out2;
+  dlmpc_stats *h_stats = nullptr;  // pinned
+  int32_t *h_err = nullptr;        // pinned [8]
+  int timing = 0;
+  bool timed_step = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+  ~dlmpc_ctx() {
+    if (h_stats) cudaFreeHost(h_stats);
+    if (h_err) cudaFreeHost(h_err);
+    for (auto &e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  int fail(int code, const std::string &msg) {
+    err = msg;
+    return code;
+  }
+  int cuda_fail(cudaError_t e, const char *what) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? DLMPC_ERR_NOMEM : DLMPC_ERR_CUDA;
+  }
+};
+
+#define CK(call, what)                                      \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return ctx->cuda_fail(e_, what); \
+  } while (0)
+
+namespace {
+
+template <class T>
+cudaError_t upload(DevBuf<T> &b, const std::vector<T> &v, cudaStream_t s) {
+  cudaError_t e = b.alloc(v.size());
+  if (e != cudaSuccess || v.empty()) return e;
+  return cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+// Hop distances from src up to max_hops (breadth-first search).
+void bfs(const Instance &I, int src, int max_hops, std::vector<int> &dist, std::vector<int> &touched) {
+  for (int v : touched) dist[v] = -1;
+  touched.clear();
+  std::vector<int> frontier{src};
+  dist[src] = 0;
+  touched.push_back(src);
+  for (int h = 0; h < max_hops && !frontier.empty(); ++h) {
+    std::vector<int> next;
+    for (int v : frontier)
+      for (int e = I.adj_ptr[v]; e < I.adj_ptr[v + 1]; ++e) {
+        const int w = I.adj_idx[e];
+        if (dist[w] < 0) {
+          dist[w] = h + 1;
+          touched.push_back(w);
+          next.push_back(w);
+        }
+      }
+    frontier.swap(next);
+  }
+}
+
+int validate(const dlmpc_problem &p, int nx, int nu, std::string &msg) {
+  char buf[256];
+  if (p.n_sub < 1 || p.nx < 1 || p.nu < 1 || p.nx > kMaxNx || p.nu > kMaxNu || p.T < 2 || p.d < 0) {
+    snprintf(buf, sizeof buf, "bad sizes n_sub=%d nx=%d nu=%d T=%d d=%d", p.n_sub, p.nx, p.nu, p.T, p.d);
+    msg = buf;
+    return DLMPC_ERR_ARG;
+  }
+  if (p.nx != nx || p.nu != nu) { msg = "all instances must share nx and nu"; return DLMPC_ERR_ARG; }
+  if (!p.adj_ptr || !p.A_diag || !p.B || !p.q || !p.r) { msg = "missing required array"; return DLMPC_ERR_ARG; }
+  if (p.adj_ptr[0] != 0) { msg = "adj_ptr[0] must be 0"; return DLMPC_ERR_ARG; }
+  const int nnz = p.adj_ptr[p.n_sub];
+  if (nnz > 0 && (!p.adj_idx || !p.A_off)) { msg = "missing adjacency arrays"; return DLMPC_ERR_ARG; }
+  for (int i = 0; i < p.n_sub; ++i) {
+    if (p.adj_ptr[i + 1] < p.adj_ptr[i]) { msg = "adj_ptr not monotone"; return DLMPC_ERR_ARG; }
+    for (int e = p.adj_ptr[i]; e < p.adj_ptr[i + 1]; ++e)
+      if (p.adj_idx[e] < 0 || p.adj_idx[e] >= p.n_sub || p.adj_idx[e] == i) {
+        msg = "adj_idx out of range or self loop";
+        return DLMPC_ERR_ARG;
+      }
+  }
+  if (!(p.rho > 0) || !(p.eps_p > 0) || !(p.eps_d > 0) || p.max_iter < 1) {
+    msg = "rho, eps_p, eps_d must be > 0 and max_iter >= 1";
+    return DLMPC_ERR_ARG;
+  }
+  for (int i = 0; i < p.n_sub * nx; ++i)
+    if (!(p.q[i] >= 0)) { msg = "q must be >= 0"; return DLMPC_ERR_ARG; }
+  for (int i = 0; i < p.n_sub * nu; ++i)
+    if (!(p.r[i] >= 0)) { msg = "r must be >= 0"; return DLMPC_ERR_ARG; }
+  if ((p.x_lo == nullptr) != (p.x_hi == nullptr) || (p.u_lo == nullptr) != (p.u_hi == nullptr)) {
+    msg = "bounds must be given in lo/hi pairs";
+    return DLMPC_ERR_ARG;
+  }
+  if (p.u_lo)
+    for (int i = 0; i < p.n_sub * nu; ++i)
+      if (!(p.u_lo[i] <= 0 && p.u_hi[i] >= 0)) { msg = "0 must lie in [u_lo, u_hi]"; return DLMPC_ERR_ARG; }
+  if (p.x_lo)
+    for (int i = 0; i < p.n_sub * nx; ++i)
+      if (!(p.x_lo[i] <= 0 && p.x_hi[i] >= 0)) { msg = "0 must lie in [x_lo, x_hi]"; return DLMPC_ERR_ARG; }
+  return 0;
+}
+
+// Restricted constraint of column patch j in the reduced variables (slot-0
+// states of the patch are fixed to e_c and moved to the right-hand side).
+// Appends CSR rows and nx right-hand sides; returns rows kept, or -1 if a row
+// without patch variables has a nonzero right-hand side (locality infeasible).
+int build_reduced(const Instance &I, int nx, int nu, int j, std::vector<int64_t> &rptr, std::vector<int32_t> &col,
+                  std::vector<double> &val, std::vector<double> &rhs_out) {
+  const auto &patch = I.patch[j];
+  const auto &ring = I.ring[j];
+  const int T = I.T;
+  const int r_sub = nx * T + nu * (T - 1);
+  const int rsr = r_sub - nx;
+  auto pos_of = [&](int i) -> int {
+    auto it = std::lower_bound(patch.begin(), patch.end(), i);
+    return (it != patch.end() && *it == i) ? int(it - patch.begin()) : -1;
+  };
+  std::vector<std::vector<double>> rhs_rows;  // per kept row: nx values
+  std::vector<std::pair<int32_t, double>> ent;
+  for (int t = 1; t < T; ++t)
+    for (int i : ring) {
+      const int pi = pos_of(i);
+      for (int a = 0; a < nx; ++a) {
+        ent.clear();
+        std::vector<double> b(nx, 0.0);
+        auto add_state = [&](int k, int pk, int slot, int bb, double coef) {
+          if (coef == 0.0 || pk < 0) return;
+          if (slot == 0) {
+            // x_0 of patch member k is e_c: moves to the right-hand side
+            if (k == j) b[bb] -= coef;
+          } else {
+            ent.emplace_back(pk * rsr + slot * nx + bb - nx, coef);
+          }
+        };
+        add_state(i, pi, t, a, 1.0);
+        for (int bb = 0; bb < nx; ++bb) add_state(i, pi, t - 1, bb, -I.A_diag[((size_t)i * nx + a) * nx + bb]);
+        for (int e = I.adj_ptr[i]; e < I.adj_ptr[i + 1]; ++e) {
+          const int k = I.adj_idx[e];
+          const int pk = pos_of(k);
+          for (int bb = 0; bb < nx; ++bb) add_state(k, pk, t - 1, bb, -I.A_off[((size_t)e * nx + a) * nx + bb]);
+        }
+        if (pi >= 0)
+          for (int e = 0; e < nu; ++e) {
+            const double coef = -I.B[((size_t)i * nx + a) * nu + e];
+            if (coef != 0.0) ent.emplace_back(pi * rsr + nx * (T - 1) + (t - 1) * nu + e, coef);
+          }
+        if (ent.empty()) {
+          for (double v : b)
+            if (v != 0.0) return -1;
+          continue;
+        }
+        std::sort(ent.begin(), ent.end());
+        // merge duplicates
+        std::vector<std::pair<int32_t, double>> merged;
+        for (auto &pr : ent) {
+          if (!merged.empty() && merged.back().first == pr.first) merged.back().second += pr.second;
+          else merged.push_back(pr);
+        }
+        for (auto &pr : merged) {
+          col.push_back(pr.first);
+          val.push_back(pr.second);
+        }
+        rptr.push_back((int64_t)col.size());
+        rhs_rows.push_back(b);
+      }
+    }
+  const int m = (int)rhs_rows.size();
+  for (int c = 0; c < nx; ++c)
+    for (int row = 0; row < m; ++row) rhs_out.push_back(rhs_rows[row][c]);
+  return m;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" int dlmpc_setup(const dlmpc_problem *probs, int32_t n_inst, void *stream, dlmpc_ctx **out) {
+  g_setup_error.clear();
+  if (!out || !probs || n_inst < 1) {
+    g_setup_error = "dlmpc_setup: null argument or n_inst < 1";
+    return DLMPC_ERR_ARG;
+  }
+  *out = nullptr;
+  auto *ctx = new (std::nothrow) dlmpc_ctx();
+  if (!ctx) return DLMPC_ERR_NOMEM;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  ctx->nx = probs[0].nx;
+  ctx->nu = probs[0].nu;
+  ctx->n_inst = n_inst;
+  const int nx = ctx->nx, nu = ctx->nu;
+  for (int b = 0; b < n_inst; ++b) {
+    std::string msg;
+    int rc = validate(probs[b], nx, nu, msg);
+    if (rc) {
+      g_setup_error = "instance " + std::to_string(b) + ": " + msg;
+      delete ctx;
+      return rc;
+    }
+  }
+  ctx->inst.resize(n_inst);
+  int sub_off = 0;
+  for (int b = 0; b < n_inst; ++b) {
+    const dlmpc_problem &p = probs[b];
+    Instance &I = ctx->inst[b];
+    I.n_sub = p.n_sub;
+    I.T = p.T;
+    I.d = p.d;
+    I.sub_off = sub_off;
+    I.item_off = sub_off;
+    sub_off += p.n_sub;
+    const int nnz = p.adj_ptr[p.n_sub];
+    I.adj_ptr.assign(p.adj_ptr, p.adj_ptr + p.n_sub + 1);
+    I.adj_idx.assign(p.adj_idx, p.adj_idx + nnz);
+    I.A_diag.assign(p.A_diag, p.A_diag + (size_t)p.n_sub * nx * nx);
+    I.A_off.assign(p.A_off, p.A_off + (size_t)nnz * nx * nx);
+    I.B.assign(p.B, p.B + (size_t)p.n_sub * nx * nu);
+    I.q.assign(p.q, p.q + (size_t)p.n_sub * nx);
+    I.r.assign(p.r, p.r + (size_t)p.n_sub * nu);
+    I.has_x = p.x_lo != nullptr;
+    I.has_u = p.u_lo != nullptr;
+    if (I.has_x) {
+      I.x_lo.assign(p.x_lo, p.x_lo + (size_t)p.n_sub * nx);
+      I.x_hi.assign(p.x_hi, p.x_hi + (size_t)p.n_sub * nx);
+    }
+    if (I.has_u) {
+      I.u_lo.assign(p.u_lo, p.u_lo + (size_t)p.n_sub * nu);
+      I.u_hi.assign(p.u_hi, p.u_hi + (size_t)p.n_sub * nu);
+    }
+    I.rho = p.rho;
+    I.eps_p = p.eps_p;
+    I.eps_d = p.eps_d;
+    I.max_iter = p.max_iter;
+    // d-hop patches and (d+1)-hop rings
+    std::vector<int> dist(p.n_sub, -1), touched;
+    I.patch.resize(p.n_sub);
+    I.ring.resize(p.n_sub);
+    for (int i = 0; i < p.n_sub; ++i) {
+      bfs(I, i, p.d + 1, dist, touched);
+      for (int v : touched) {
+        if (dist[v] <= p.d) I.patch[i].push_back(v);
+        I.ring[i].push_back(v);
+      }
+      std::sort(I.patch[i].begin(), I.patch[i].end());
+      std::sort(I.ring[i].begin(), I.ring[i].end());
+    }
+  }
+  ctx->n_sub = sub_off;
+  // items, exchange layout, reduced constraints
+  ctx->items.resize(ctx->n_sub);
+  ctx->np_of.resize(ctx->n_sub);
+  ctx->g_off.resize(ctx->n_sub);
+  int64_t goff = 0, st_off = 0, q_off = 0;
+  for (int b = 0; b < n_inst; ++b) {
+    const Instance &I = ctx->inst[b];
+    const int r_sub = nx * I.T + nu * (I.T - 1);
+    for (int i = 0; i < I.n_sub; ++i) {
+      const int g = I.sub_off + i;
+      ctx->np_of[g] = (int)I.patch[i].size();
+      ctx->g_off[g] = goff;
+      goff += (int64_t)ctx->np_of[g] * r_sub;
+    }
+  }
+  ctx->g_floats = goff;
+  ctx->zrow_ptr.clear();
+  ctx->kub.resize(ctx->n_sub);
+  ctx->rhs_off.resize(ctx->n_sub);
+  for (int b = 0; b < n_inst; ++b) {
+    const Instance &I = ctx->inst[b];
+    const int r_sub = nx * I.T + nu * (I.T - 1);
+    for (int j = 0; j < I.n_sub; ++j) {
+      const int g = I.sub_off + j;
+      Item &it = ctx->items[g];
+      it.inst = b;
+      it.sub = g;
+      it.n_mem = (int)I.patch[j].size();
+      it.mem_off = (int)ctx->members.size();
+      it.self_pos = int(std::lower_bound(I.patch[j].begin(), I.patch[j].end(), j) - I.patch[j].begin());
+      it.r_sub = r_sub;
+      it.T = I.T;
+      it.dred = (r_sub - nx) * it.n_mem;
+      it.dred_pad = (int)round_up(it.dred, 4);
+      it.st_off = st_off;
+      st_off += (int64_t)nx * r_sub * it.n_mem;
+      it.q_off = q_off;
+      q_off += (int64_t)nx * it.dred_pad;
+      for (int m : I.patch[j]) {
+        ctx->members.push_back(I.sub_off + m);
+        const auto &pm = I.patch[m];
+        ctx->rev_slot.push_back(int(std::lower_bound(pm.begin(), pm.end(), j) - pm.begin()));
+      }
+      it.z_off = (int64_t)ctx->zrow_ptr.size();
+      ctx->zrow_ptr.push_back((int64_t)ctx->zcol.size());
+      ctx->rhs_off[g] = (int64_t)ctx->rhs.size();
+      const int m = build_reduced(I, nx, nu, j, ctx->zrow_ptr, ctx->zcol, ctx->zval, ctx->rhs);
+      if (m < 0) {
+        g_setup_error = "instance " + std::to_string(b) + " subsystem " + std::to_string(j) +
+                        ": locality constraint infeasible (row without patch variables has nonzero RHS)";
+        delete ctx;
+        return DLMPC_ERR_INFEASIBLE_LOCALITY;
+      }
+      it.mrows = m;
+      ctx->kub[g] = std::max(1, nu * (I.T - 1) * it.n_mem);
+      it.k = 0;
+      it.kpad = 1;
+      ctx->max_dcol = std::max(ctx->max_dcol, r_sub * it.n_mem);
+    }
+  }
+  ctx->state_floats = st_off;
+  ctx->q_floats = q_off;
+  *out = ctx;
+  return DLMPC_OK;
+}
+
+namespace {
+
+int upload_static(dlmpc_ctx *ctx) {
+  const int nx = ctx->nx, nu = ctx->nu;
+  cudaStream_t s = ctx->stream;
+  std::vector<float> qw, rw, xlo, xhi, ulo, uhi, rho, epsp, epsd;
+  std::vector<double> Ad, Ao, Bm;
+  std::vector<int32_t> aptr{0}, aidx, inst_item_ptr{0};
+  for (const Instance &I : ctx->inst) {
+    const float inf = std::numeric_limits<float>::infinity();
+    for (int i = 0; i < I.n_sub; ++i) {
+      for (int a = 0; a < nx; ++a) {
+        qw.push_back((float)I.q[(size_t)i * nx + a]);
+        xlo.push_back(I.has_x ? (float)I.x_lo[(size_t)i * nx + a] : -inf);
+        xhi.push_back(I.has_x ? (float)I.x_hi[(size_t)i * nx + a] : inf);
+      }
+      for (int e = 0; e < nu; ++e) {
+        rw.push_back((float)I.r[(size_t)i * nu + e]);
+        ulo.push_back(I.has_u ? (float)I.u_lo[(size_t)i * nu + e] : -inf);
+        uhi.push_back(I.has_u ? (float)I.u_hi[(size_t)i * nu + e] : inf);
+      }
+      for (int e = I.adj_ptr[i]; e < I.adj_ptr[i + 1]; ++e) aidx.push_back(I.sub_off + I.adj_idx[e]);
+      aptr.push_back((int32_t)aidx.size());
+    }
+    Ad.insert(Ad.end(), I.A_diag.begin(), I.A_diag.end());
+    Ao.insert(Ao.end(), I.A_off.begin(), I.A_off.end());
+    Bm.insert(Bm.end(), I.B.begin(), I.B.end());
+    rho.push_back((float)I.rho);
+    epsp.push_back((float)I.eps_p);
+    epsd.push_back((float)I.eps_d);
+    inst_item_ptr.push_back(I.item_off + I.n_sub);
+  }
+  CK(upload(ctx->d_qw, qw, s), "upload qw");
+  CK(upload(ctx->d_rw, rw, s), "upload rw");
+  CK(upload(ctx->d_xlo, xlo, s), "upload xlo");
+  CK(upload(ctx->d_xhi, xhi, s), "upload xhi");
+  CK(upload(ctx->d_ulo, ulo, s), "upload ulo");
+  CK(upload(ctx->d_uhi, uhi, s), "upload uhi");
+  CK(upload(ctx->d_rho, rho, s), "upload rho");
+  CK(upload(ctx->d_epsp, epsp, s), "upload eps");
+  CK(upload(ctx->d_epsd, epsd, s), "upload eps");
+  CK(upload(ctx->d_Adiag, Ad, s), "upload A");
+  CK(upload(ctx->d_Aoff, Ao, s), "upload A");
+  CK(upload(ctx->d_B, Bm, s), "upload B");
+  CK(upload(ctx->d_adj_ptr, aptr, s), "upload adjacency");
+  CK(upload(ctx->d_adj_idx, aidx, s), "upload adjacency");
+  CK(upload(ctx->d_inst_item_ptr, inst_item_ptr, s), "upload instance offsets");
+  CK(upload(ctx->d_members, ctx->members, s), "upload members");
+  CK(upload(ctx->d_rev, ctx->rev_slot, s), "upload rev");
+  CK(upload(ctx->d_np, ctx->np_of, s), "upload np");
+  CK(upload(ctx->d_goff, ctx->g_off, s), "upload goff");
+  std::vector<int32_t> sub_off;
+  for (const Instance &I : ctx->inst) sub_off.push_back(I.sub_off);
+  sub_off.push_back(ctx->n_sub);
+  CK(upload(ctx->d_sub_off, sub_off, s), "upload sub offsets");
+  CK(ctx->d_psi.alloc(ctx->state_floats), "alloc Psi");
+  CK(ctx->d_lam.alloc(ctx->state_floats), "alloc Lambda");
+  CK(cudaMemsetAsync(ctx->d_psi.p, 0, ctx->state_floats * 4, s), "memset");
+  CK(cudaMemsetAsync(ctx->d_lam.p, 0, ctx->state_floats * 4, s), "memset");
+  CK(ctx->d_G0.alloc(ctx->g_floats), "alloc exchange");
+  CK(ctx->d_G1.alloc(ctx->g_floats), "alloc exchange");
+  CK(ctx->d_S.alloc(ctx->n_sub), "alloc S");
+  CK(ctx->d_item_r.alloc(ctx->n_sub), "alloc residuals");
+  CK(ctx->d_item_s.alloc(ctx->n_sub), "alloc residuals");
+  CK(ctx->d_bar.alloc(1), "alloc barrier");
+  CK(ctx->d_notconv.alloc(3 * (ctx->n_inst + 1)), "alloc conv");
+  CK(ctx->d_inst_iters.alloc(ctx->n_inst), "alloc iters");
+  CK(ctx->d_err.alloc(8), "alloc err");
+  CK(ctx->d_stats.alloc(ctx->n_inst), "alloc stats");
+  CK(ctx->d_x.alloc((size_t)ctx->n_sub * nx), "alloc staging");
+  CK(ctx->d_u.alloc((size_t)ctx->n_sub * nu), "alloc staging");
+  CK(ctx->d_xn.alloc((size_t)ctx->n_sub * nx), "alloc staging");
+  CK(cudaMallocHost(&ctx->h_stats, sizeof(dlmpc_stats) * ctx->n_inst), "alloc pinned");
+  CK(cudaMallocHost(&ctx->h_err, sizeof(int32_t) * 8), "alloc pinned");
+  return 0;
+}
+
+// Longest-processing-time assignment of column patches to CTAs.
+void assign_work(dlmpc_ctx *ctx, int grid) {
+  const int n = ctx->n_sub;
+  std::vector<double> cost(n);
+  for (int g = 0; g < n; ++g) {
+    const Item &it = ctx->items[g];
+    cost[g] = (double)it.dred * (2.0 * it.k + 4.0 * ctx->nx) + 8.0 * it.r_sub * it.n_mem + 2000.0;
+  }
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  using P = std::pair<double, int>;
+  std::priority_queue<P, std::vector<P>, std::greater<P>> heap;
+  for (int b = 0; b < grid; ++b) heap.push({0.0, b});
+  std::vector<std::vector<int32_t>> bins(grid);
+  for (int g : order) {
+    auto top = heap.top();
+    heap.pop();
+    bins[top.second].push_back(g);
+    heap.push({top.first + cost[g], top.second});
+  }
+  ctx->cta_ptr.assign(1, 0);
+  ctx->cta_items.clear();
+  for (auto &bn : bins) {
+    std::sort(bn.begin(), bn.end());
+    ctx->cta_items.insert(ctx->cta_items.end(), bn.begin(), bn.end());
+    ctx->cta_ptr.push_back((int32_t)ctx->cta_items.size());
+  }
+}
+
+int configure_launch(dlmpc_ctx *ctx) {
+  int dev = 0, sms = 0, smem_optin = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
+  CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
+  int smem_sm = 0;
+  CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev), "attr");
+  int64_t full_n = 4;
+  for (const Item &it : ctx->items) full_n = std::max<int64_t>(full_n, (int64_t)it.dred_pad * it.kpad);
+  const size_t fixed = sweep_smem_bytes(ctx->nx, 0, ctx->max_dcol, ctx->max_kpad);
+  // Largest CTA count per SM that keeps every patch operator resident in
+  // shared memory; if none does, one CTA per SM streams N in row chunks.
+  int64_t best_n = 0;
+  const int want_c = ctx->ctas_per_sm;
+  for (int c = 8; c >= 1; --c) {
+    if (want_c > 0 && c != want_c) continue;
+    const int64_t per = std::min<int64_t>(smem_optin, (int64_t)smem_sm / c - 1024) - (int64_t)fixed;
+    if (per / 4 >= full_n) { best_n = full_n; break; }
+    if (c == 1 || want_c > 0) best_n = std::max<int64_t>(0, per / 4);
+  }
+  if (best_n < 4 * ctx->max_kpad)
+    return ctx->fail(DLMPC_ERR_ARG, "patch operators too large for the shared-memory budget");
+  if (ctx->smem_opt > 0) best_n = std::min<int64_t>(best_n, (ctx->smem_opt - (int64_t)fixed) / 4);
+  best_n = std::max<int64_t>(best_n & ~int64_t(3), 4 * ctx->max_kpad);
+  best_n = std::min<int64_t>(best_n, round_up(full_n, 4));
+  ctx->smem_n_floats = (int)best_n;
+  ctx->smem = sweep_smem_bytes(ctx->nx, ctx->smem_n_floats, ctx->max_dcol, ctx->max_kpad);
+  const void *fn = admm_kernel_ptr(ctx->nx);
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem), "smem attr");
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sweep_threads(), ctx->smem), "occupancy");
+  if (occ < 1) return ctx->fail(DLMPC_ERR_ARG, "sweep kernel cannot be resident");
+  if (want_c > 0) occ = std::min(occ, want_c);
+  ctx->grid = std::min(ctx->n_sub, sms * occ);
+  assign_work(ctx, ctx->grid);
+  CK(upload(ctx->d_cta_ptr, ctx->cta_ptr, ctx->stream), "upload cta_ptr");
+  CK(upload(ctx->d_cta_items, ctx->cta_items, ctx->stream), "upload cta_items");
+  return 0;
+}
+
+}  // namespace
+
+extern "C" int dlmpc_precompute(dlmpc_ctx *ctx) {
+  if (!ctx) return DLMPC_ERR_ARG;
+  const int nx = ctx->nx;
+  cudaStream_t s = ctx->stream;
+  int rc = upload_static(ctx);
+  if (rc) return rc;
+  // scratch layout for the factorisation: N with stride k_ub
+  std::vector<Item> scratch = ctx->items;
+  int64_t off = 0, max_D = 1, max_m = 1;
+  for (int g = 0; g < ctx->n_sub; ++g) {
+    Item &it = scratch[g];
+    it.k = ctx->kub[g];
+    it.kpad = ctx->kub[g];
+    it.n_off = off;
+    off += round_up((int64_t)it.dred_pad * it.kpad, 4);
+    max_D = std::max<int64_t>(max_D, it.dred);
+    max_m = std::max<int64_t>(max_m, it.mrows);
+  }
+  DevBuf<Item> d_scr;
+  DevBuf<float> d_Nscr;
+  DevBuf<int64_t> d_zptr, d_rhs_off;
+  DevBuf<int32_t> d_zcol, d_rank, d_null;
+  DevBuf<double> d_zval, d_rhs, d_ws, d_feas;
+  CK(upload(d_scr, scratch, s), "upload items");
+  CK(d_Nscr.alloc(off), "alloc N scratch");
+  CK(ctx->d_q.alloc(ctx->q_floats), "alloc q");
+  CK(upload(d_zptr, ctx->zrow_ptr, s), "upload Z");
+  CK(upload(d_zcol, ctx->zcol, s), "upload Z");
+  CK(upload(d_zval, ctx->zval, s), "upload Z");
+  CK(upload(d_rhs, ctx->rhs, s), "upload rhs");
+  CK(upload(d_rhs_off, ctx->rhs_off, s), "upload rhs");
+  CK(d_rank.alloc(ctx->n_sub), "alloc");
+  CK(d_null.alloc(ctx->n_sub), "alloc");
+  CK(d_feas.alloc(ctx->n_sub), "alloc");
+  const int64_t ws_stride = round_up(max_D * max_m + (3 + nx) * max_m + 8 * max_D + max_m / 2 + 8, 32);
+  int dev = 0, sms = 1;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
+  const int64_t budget = (int64_t)4 << 30;
+  int conc = (int)std::min<int64_t>({(int64_t)ctx->n_sub, (int64_t)sms * 4, std::max<int64_t>(1, budget / (ws_stride * 8))});
+  CK(d_ws.alloc((size_t)conc * ws_stride), "alloc factor workspace");
+  FactorParams fp{};
+  fp.items = d_scr.p;
+  fp.n_items = ctx->n_sub;
+  fp.zrow_ptr = d_zptr.p;
+  fp.zcol = d_zcol.p;
+  fp.zval = d_zval.p;
+  fp.rhs = d_rhs.p;
+  fp.rhs_off = d_rhs_off.p;
+  fp.ws = d_ws.p;
+  fp.ws_stride = ws_stride;
+  fp.Nmat = d_Nscr.p;
+  fp.qvec = ctx->d_q.p;
+  fp.feas = d_feas.p;
+  fp.rank = d_rank.p;
+  fp.nullity = d_null.p;
+  fp.nx = nx;
+  fp.use_smem = 0;
+  for (int b = 0; b < ctx->n_sub; b += conc) {
+    fp.item_begin = b;
+    CK(launch_factor(fp, std::min(conc, ctx->n_sub - b), 0, s), "factor_kernel");
+  }
+  std::vector<double> feas(ctx->n_sub);
+  std::vector<int32_t> nul(ctx->n_sub);
+  CK(cudaMemcpyAsync(feas.data(), d_feas.p, 8 * feas.size(), cudaMemcpyDeviceToHost, s), "D2H");
+  CK(cudaMemcpyAsync(nul.data(), d_null.p, 4 * nul.size(), cudaMemcpyDeviceToHost, s), "D2H");
+  CK(cudaStreamSynchronize(s), "factorisation");
+  for (int g = 0; g < ctx->n_sub; ++g) {
+    if (!(feas[g] <= 1e-9)) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "subsystem %d: ||Z q - e|| = %.3e (locality infeasible)", g, feas[g]);
+      return ctx->fail(DLMPC_ERR_INFEASIBLE_LOCALITY, buf);
+    }
+    if (nul[g] > ctx->kub[g]) return ctx->fail(DLMPC_ERR_ARG, "null-space dimension above its structural bound");
+    if (nul[g] > 2 * sweep_threads()) return ctx->fail(DLMPC_ERR_ARG, "null-space dimension above 512");
+  }
+  // packed layout: odd stride kpad, 16-byte aligned items
+  int64_t noff = 0;
+  ctx->max_kpad = 1;
+  for (int g = 0; g < ctx->n_sub; ++g) {
+    Item &it = ctx->items[g];
+    it.k = nul[g];
+    it.kpad = (it.k % 2 == 1) ? it.k : it.k + 1;
+    it.n_off = noff;
+    noff += round_up((int64_t)it.dred_pad * it.kpad, 4);
+    ctx->max_kpad = std::max(ctx->max_kpad, it.kpad);
+  }
+  ctx->n_floats = noff;
+  CK(upload(ctx->d_items, ctx->items, s), "upload items");
+  CK(ctx->d_N.alloc(noff), "alloc N");
+  CK(launch_repack(d_scr.p, ctx->d_items.p, ctx->n_sub, d_Nscr.p, ctx->d_N.p, s), "repack_kernel");
+  CK(cudaStreamSynchronize(s), "repack");
+  rc = configure_launch(ctx);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s), "precompute");
+  ctx->precomputed = true;
+  return DLMPC_OK;
+}
+
+namespace {
+
+int run_step(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_dev, int warm, dlmpc_stats *stats) {
+  if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
+  if (warm != DLMPC_WARM_COLD && warm != DLMPC_WARM_PREVIOUS)
+    return ctx->fail(DLMPC_ERR_ARG, "unsupported warm-start mode");
+  cudaStream_t s = ctx->stream;
+  if (ctx->export_phi && ctx->d_phi.n != (size_t)ctx->state_floats) {
+    CK(ctx->d_phi.alloc(ctx->state_floats), "alloc Phi");
+    CK(cudaMemsetAsync(ctx->d_phi.p, 0, ctx->state_floats * 4, s), "memset");
+  }
+  ctx->timed_step = false;
+  if (ctx->timing) {
+    for (auto &e : ctx->ev)
+      if (!e) CK(cudaEventCreate(&e), "cudaEventCreate");
+    CK(cudaEventRecord(ctx->ev[0], s), "event");
+  }
+  CK(cudaMemsetAsync(ctx->d_bar.p, 0, 4, s), "memset");
+  CK(cudaMemsetAsync(ctx->d_err.p, 0, 32, s), "memset");
+  Params P{};
+  P.items = ctx->d_items.p;
+  P.n_items = ctx->n_sub;
+  P.cta_ptr = ctx->d_cta_ptr.p;
+  P.cta_items = ctx->d_cta_items.p;
+  P.members = ctx->d_members.p;
+  P.rev_slot = ctx->d_rev.p;
+  P.np_of = ctx->d_np.p;
+  P.g_off = ctx->d_goff.p;
+  P.Nmat = ctx->d_N.p;
+  P.qvec = ctx->d_q.p;
+  P.Psi = ctx->d_psi.p;
+  P.Lam = ctx->d_lam.p;
+  P.Phi = ctx->export_phi ? ctx->d_phi.p : nullptr;
+  P.G0 = ctx->d_G0.p;
+  P.G1 = ctx->d_G1.p;
+  P.S = ctx->d_S.p;
+  P.x = x_dev;
+  P.u = u_dev;
+  P.x_next = xn_dev;
+  P.qw = ctx->d_qw.p;
+  P.rw = ctx->d_rw.p;
+  P.xlo = ctx->d_xlo.p;
+  P.xhi = ctx->d_xhi.p;
+  P.ulo = ctx->d_ulo.p;
+  P.uhi = ctx->d_uhi.p;
+  P.Adiag = ctx->d_Adiag.p;
+  P.Aoff = ctx->d_Aoff.p;
+  P.adj_ptr = ctx->d_adj_ptr.p;
+  P.adj_idx = ctx->d_adj_idx.p;
+  P.Bm = ctx->d_B.p;
+  P.n_inst = ctx->n_inst;
+  P.rho_i = ctx->d_rho.p;
+  P.epsp_i = ctx->d_epsp.p;
+  P.epsd_i = ctx->d_epsd.p;
+  P.bar = ctx->d_bar.p;
+  P.notconv = ctx->d_notconv.p;
+  P.inst_iters = ctx->d_inst_iters.p;
+  P.item_r = ctx->d_item_r.p;
+  P.item_s = ctx->d_item_s.p;
+  P.err = ctx->d_err.p;
+  int max_iter = 1;
+  for (const Instance &I : ctx->inst) max_iter = std::max(max_iter, I.max_iter);
+  P.max_iter = ctx->max_iter_override > 0 ? ctx->max_iter_override : max_iter;
+  P.fixed_iters = ctx->fixed_iters;
+  P.warm = warm;
+  P.nx = ctx->nx;
+  P.nu = ctx->nu;
+  P.timeout_ns = (unsigned long long)(ctx->timeout_ms * 1e6);
+  P.smem_n_floats = ctx->smem_n_floats;
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s), "event");
+  CK(launch_admm(ctx->nx, P, ctx->max_dcol, ctx->max_kpad, ctx->grid, ctx->smem, s), "admm_kernel launch");
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s), "event");
+  if (!stats) {
+    if (ctx->timing) {
+      CK(cudaEventRecord(ctx->ev[3], s), "event");
+      ctx->timed_step = true;
+    }
+    return DLMPC_OK;
+  }
+  CK(launch_stats(ctx->d_inst_item_ptr.p, ctx->n_inst, ctx->d_item_r.p, ctx->d_item_s.p, ctx->d_inst_iters.p,
+                  ctx->d_err.p, ctx->fixed_iters, ctx->d_epsp.p, ctx->d_epsd.p, ctx->d_stats.p, s),
+     "stats_kernel");
+  CK(cudaMemcpyAsync(ctx->h_stats, ctx->d_stats.p, sizeof(dlmpc_stats) * ctx->n_inst, cudaMemcpyDeviceToHost, s),
+     "D2H stats");
+  CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err.p, 32, cudaMemcpyDeviceToHost, s), "D2H err");
+  if (ctx->timing) {
+    CK(cudaEventRecord(ctx->ev[3], s), "event");
+    ctx->timed_step = true;
+  }
+  CK(cudaStreamSynchronize(s), "step");
+  if (ctx->h_err[0] != 0) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "device error %d (cta %d, iteration %d, aux %d)", ctx->h_err[0], ctx->h_err[1],
+             ctx->h_err[2], ctx->h_err[3]);
+    return ctx->fail(ctx->h_err[0], buf);
+  }
+  int worst = DLMPC_OK;
+  for (int b = 0; b < ctx->n_inst; ++b) {
+    stats[b] = ctx->h_stats[b];
+    if (stats[b].status != DLMPC_OK) worst = stats[b].status;
+  }
+  return worst;
+}
+
+}  // namespace
+
+extern "C" int dlmpc_step(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *x_next_dev, int32_t warm,
+                          dlmpc_stats *stats) {
+  if (!ctx || !x_dev || !u_dev) return ctx ? ctx->fail(DLMPC_ERR_ARG, "null x or u") : DLMPC_ERR_ARG;
+  return run_step(ctx, x_dev, u_dev, x_next_dev, warm, stats);
+}
+
+extern "C" int dlmpc_step_host(dlmpc_ctx *ctx, const float *x, float *u, float *x_next, int32_t warm,
+                               dlmpc_stats *stats) {
+  if (!ctx || !x || !u) return ctx ? ctx->fail(DLMPC_ERR_ARG, "null x or u") : DLMPC_ERR_ARG;
+  if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
+  cudaStream_t s = ctx->stream;
+  const size_t nxb = (size_t)ctx->n_sub * ctx->nx * 4, nub = (size_t)ctx->n_sub * ctx->nu * 4;
+  CK(cudaMemcpyAsync(ctx->d_x.p, x, nxb, cudaMemcpyHostToDevice, s), "H2D x");
+  int rc = run_step(ctx, ctx->d_x.p, ctx->d_u.p, x_next ? ctx->d_xn.p : nullptr, warm, stats);
+  if (rc < 0) return rc;
+  CK(cudaMemcpyAsync(u, ctx->d_u.p, nub, cudaMemcpyDeviceToHost, s), "D2H u");
+  if (x_next) CK(cudaMemcpyAsync(x_next, ctx->d_xn.p, nxb, cudaMemcpyDeviceToHost, s), "D2H x_next");
+  CK(cudaStreamSynchronize(s), "step_host");
+  return rc;
+}
+
+extern "C" int dlmpc_solve_batch(dlmpc_ctx *ctx, const float *const *x_dev, float *const *u_dev,
+                                 float *const *x_next_dev, int32_t warm, dlmpc_stats *stats) {
+  if (!ctx || !x_dev || !u_dev) return ctx ? ctx->fail(DLMPC_ERR_ARG, "null pointer table") : DLMPC_ERR_ARG;
+  if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
+  cudaStream_t s = ctx->stream;
+  const int n = ctx->n_inst;
+  if (ctx->d_ptr_in.n != (size_t)n) {
+    CK(ctx->d_ptr_in.alloc(n), "alloc");
+    CK(ctx->d_ptr_out.alloc(n), "alloc");
+    CK(ctx->d_ptr_out2.alloc(n), "alloc");
+  }
+  std::vector<float *> xn(n, nullptr);
+  if (x_next_dev)
+    for (int b = 0; b < n; ++b) xn[b] = x_next_dev[b];
+  CK(cudaMemcpyAsync(ctx->d_ptr_in.p, x_dev, sizeof(float *) * n, cudaMemcpyHostToDevice, s), "H2D");
+  CK(cudaMemcpyAsync(ctx->d_ptr_out.p, u_dev, sizeof(float *) * n, cudaMemcpyHostToDevice, s), "H2D");
+  CK(cudaMemcpyAsync(ctx->d_ptr_out2.p, xn.data(), sizeof(float *) * n, cudaMemcpyHostToDevice, s), "H2D");
+  CK(launch_gather(ctx->d_ptr_in.p, ctx->d_sub_off.p, n, ctx->nx, ctx->d_x.p, s), "gather");
+  int rc = run_step(ctx, ctx->d_x.p, ctx->d_u.p, x_next_dev ? ctx->d_xn.p : nullptr, warm, stats);
+  if (rc < 0) return rc;
+  CK(launch_scatter(ctx->d_u.p, ctx->d_sub_off.p, n, ctx->nu, ctx->d_ptr_out.p, s), "scatter");
+  if (x_next_dev) CK(launch_scatter(ctx->d_xn.p, ctx->d_sub_off.p, n, ctx->nx, ctx->d_ptr_out2.p, s), "scatter");
+  if (stats) CK(cudaStreamSynchronize(s), "solve_batch");
+  return rc;
+}
+
+extern "C" int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value) {
+  if (!ctx) return DLMPC_ERR_ARG;
+  switch (key) {
+    case DLMPC_OPT_FIXED_ITERS: ctx->fixed_iters = (int)value; return 0;
+    case DLMPC_OPT_MAX_ITER: ctx->max_iter_override = (int)value; return 0;
+    case DLMPC_OPT_TIMEOUT_MS:
+      if (!(value > 0)) return ctx->fail(DLMPC_ERR_ARG, "timeout must be > 0");
+      ctx->timeout_ms = value;
+      return 0;
+    case DLMPC_OPT_EXPORT_PHI: ctx->export_phi = value != 0; return 0;
+    case DLMPC_OPT_TIMING: ctx->timing = value != 0; return 0;
+    case DLMPC_OPT_CTAS_PER_SM:
+    case DLMPC_OPT_SMEM_BYTES: {
+      if (key == DLMPC_OPT_CTAS_PER_SM) ctx->ctas_per_sm = (int)value;
+      else ctx->smem_opt = (int)value;
+      if (ctx->precomputed) return configure_launch(ctx);
+      return 0;
+    }
+  }
+  return ctx->fail(DLMPC_ERR_ARG, "unknown option");
+}
+
+extern "C" int dlmpc_get_info(dlmpc_ctx *ctx, dlmpc_info *info) {
+  if (!ctx || !info) return DLMPC_ERR_ARG;
+  info->n_inst = ctx->n_inst;
+  info->n_sub_total = ctx->n_sub;
+  info->nx = ctx->nx;
+  info->nu = ctx->nu;
+  info->n_items = ctx->n_sub;
+  info->max_dcol = ctx->max_dcol;
+  int maxk = 0;
+  for (const Item &it : ctx->items) maxk = std::max(maxk, it.k);
+  info->max_nullity = maxk;
+  info->state_floats = ctx->state_floats;
+  info->operator_bytes = ctx->n_floats * 4;
+  info->offset_bytes = ctx->q_floats * 4;
+  info->exchange_floats = ctx->g_floats;
+  info->grid_ctas = ctx->grid;
+  info->threads_per_cta = sweep_threads();
+  info->smem_bytes = (int32_t)ctx->smem;
+  return 0;
+}
+
+extern "C" int dlmpc_get_state(dlmpc_ctx *ctx, float *phi_dev, float *psi_dev, float *lam_dev) {
+  if (!ctx) return DLMPC_ERR_ARG;
+  cudaStream_t s = ctx->stream;
+  const size_t bytes = (size_t)ctx->state_floats * 4;
+  if (phi_dev) {
+    if (!ctx->d_phi.p) return ctx->fail(DLMPC_ERR_ARG, "Phi export is off (DLMPC_OPT_EXPORT_PHI)");
+    CK(cudaMemcpyAsync(phi_dev, ctx->d_phi.p, bytes, cudaMemcpyDeviceToDevice, s), "copy Phi");
+  }
+  if (psi_dev) CK(cudaMemcpyAsync(psi_dev, ctx->d_psi.p, bytes, cudaMemcpyDeviceToDevice, s), "copy Psi");
+  if (lam_dev) CK(cudaMemcpyAsync(lam_dev, ctx->d_lam.p, bytes, cudaMemcpyDeviceToDevice, s), "copy Lambda");
+  return 0;
+}
+
+extern "C" int dlmpc_set_state(dlmpc_ctx *ctx, const float *psi_dev, const float *lam_dev) {
+  if (!ctx || !psi_dev || !lam_dev) return DLMPC_ERR_ARG;
+  if (!ctx->d_psi.p) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
+  cudaStream_t s = ctx->stream;
+  const size_t bytes = (size_t)ctx->state_floats * 4;
+  CK(cudaMemcpyAsync(ctx->d_psi.p, psi_dev, bytes, cudaMemcpyDeviceToDevice, s), "set Psi");
+  CK(cudaMemcpyAsync(ctx->d_lam.p, lam_dev, bytes, cudaMemcpyDeviceToDevice, s), "set Lambda");
+  return 0;
+}
+
+extern "C" int dlmpc_get_patch(dlmpc_ctx *ctx, int32_t j, int32_t *members, int32_t cap) {
+  if (!ctx || j < 0 || j >= ctx->n_sub) return DLMPC_ERR_ARG;
+  const Item &it = ctx->items[j];
+  if (members) {
+    if (cap < it.n_mem) return ctx->fail(DLMPC_ERR_ARG, "capacity too small");
+    for (int e = 0; e < it.n_mem; ++e) members[e] = ctx->members[it.mem_off + e];
+  }
+  return it.n_mem;
+}
+
+extern "C" int dlmpc_get_operator(dlmpc_ctx *ctx, int32_t j, double *N, int32_t n_cap, double *q, int32_t q_cap) {
+  if (!ctx || j < 0 || j >= ctx->n_sub) return DLMPC_ERR_ARG;
+  if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
+  const Item &it = ctx->items[j];
+  const int nx = ctx->nx, dcol = it.r_sub * it.n_mem, rsr = it.r_sub - nx;
+  if ((N && n_cap < dcol * it.k) || (q && q_cap < nx * dcol)) return ctx->fail(DLMPC_ERR_ARG, "capacity too small");
+  std::vector<float> hn((size_t)it.dred_pad * it.kpad), hq((size_t)nx * it.dred_pad);
+  CK(cudaMemcpyAsync(hn.data(), ctx->d_N.p + it.n_off, hn.size() * 4, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  CK(cudaMemcpyAsync(hq.data(), ctx->d_q.p + it.q_off, hq.size() * 4, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  CK(cudaStreamSynchronize(ctx->stream), "get_operator");
+  auto full = [&](int red) { const int mpos = red / rsr; return mpos * it.r_sub + nx + (red - mpos * rsr); };
+  if (N) {
+    std::fill(N, N + (size_t)dcol * it.k, 0.0);
+    for (int red = 0; red < it.dred; ++red)
+      for (int a = 0; a < it.k; ++a) N[(size_t)full(red) * it.k + a] = hn[(size_t)red * it.kpad + a];
+  }
+  if (q) {
+    std::fill(q, q + (size_t)nx * dcol, 0.0);
+    for (int c = 0; c < nx; ++c) {
+      q[(size_t)c * dcol + it.self_pos * it.r_sub + c] = 1.0;
+      for (int red = 0; red < it.dred; ++red) q[(size_t)c * dcol + full(red)] = hq[(size_t)c * it.dred_pad + red];
+    }
+  }
+  return it.k;
+}
+
+extern "C" int dlmpc_get_timing(dlmpc_ctx *ctx, float *ms) {
+  if (!ctx || !ms) return DLMPC_ERR_ARG;
+  if (!ctx->timed_step) return ctx->fail(DLMPC_ERR_ARG, "no timed step (enable DLMPC_OPT_TIMING)");
+  CK(cudaEventSynchronize(ctx->ev[3]), "event sync");
+  CK(cudaEventElapsedTime(&ms[0], ctx->ev[1], ctx->ev[2]), "elapsed");
+  CK(cudaEventElapsedTime(&ms[1], ctx->ev[0], ctx->ev[3]), "elapsed");
+  return 0;
+}
+
+extern "C" const char *dlmpc_last_error(dlmpc_ctx *ctx) {
+  if (!ctx) return g_setup_error.c_str();
+  return ctx->err.c_str();
+}
+
+extern "C" void dlmpc_destroy(dlmpc_ctx *ctx) { delete ctx; }

@@ -1,0 +1,182 @@
+"""CUDA path against the FP64 oracle on the same seeded inputs.
+
+Parity modes:
+  fixed-K  both sides run exactly K ADMM iterations from the same start;
+           ||X_gpu - X_oracle||_F / ||X_oracle||_F <= 1e-4 for Phi, Psi,
+           Lambda (column-owned layout) and u(0).
+  stopped  Conv on; u(tau) within 1e-4 relative (absolute floor 1e-7 per
+           entry scaled by ||u||) and the iteration counts reported.
+Every call goes through the C ABI (libdlmpc.so) via the ctypes binding.
+"""
+import numpy as np
+import pytest
+
+from oracle import dlmpc_oracle as O
+from paper_2103_14990_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).reshape(-1)
+    b = np.asarray(b, np.float64).reshape(-1)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / max(nb, 1e-30)
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def gpu_solver(probs, torch):
+    import paper_2103_14990_gb300 as pkg
+    return pkg.Solver(probs)
+
+
+def run_fixed(solver, torch, x0, K, warm=0):
+    import paper_2103_14990_gb300 as pkg
+    solver.set_option(pkg.OPT_FIXED_ITERS, K)
+    solver.set_option(pkg.OPT_EXPORT_PHI, 1)
+    x = torch.tensor(np.asarray(x0, np.float32).reshape(-1, solver.nx), device="cuda")
+    u = torch.zeros(solver.n_sub, solver.nu, device="cuda")
+    xn = torch.zeros_like(x)
+    rc, st = solver.step(x, u, xn, warm=warm)
+    phi, psi, lam = solver.get_state(phi=True)
+    torch.cuda.synchronize()
+    solver.set_option(pkg.OPT_FIXED_ITERS, 0)
+    return (rc, st, phi.cpu().numpy(), psi.cpu().numpy(), lam.cpu().numpy(), u.cpu().numpy(),
+            xn.cpu().numpy())
+
+
+SMALL = {
+    "chain10": lambda: I.chain10(),
+    "chain16_T10_d3_box": lambda: I.make_instance(16, 10, 3, seed=1, boxes=True, x0_dist="uniform"),
+    "grid5x5_T6_d2_box": lambda: I.make_instance(25, 6, 2, graph="grid", seed=2, boxes=True),
+    "grid3x4_T4_d1": lambda: I.make_instance(12, 4, 1, graph="grid", seed=4, boxes=False, x0_dist="normal"),
+    "chain1_T2": lambda: I.make_instance(1, 2, 1, seed=5, boxes=True),
+    "chain7_T5_d6_nolocality": lambda: I.make_instance(7, 5, 6, seed=6, boxes=False, x0_dist="normal"),
+}
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_operator_matches_oracle_projector(name, torch):
+    p = SMALL[name]()
+    s = gpu_solver([p], torch)
+    for j in range(p.n_sub):
+        N, q = s.operator(j)
+        blk = O.column_block(p, j)
+        assert N.shape[1] == blk.P.shape[0] - blk.rank          # same nullity
+        assert np.max(np.abs(N @ N.T - blk.P)) < 2e-6            # N N^T = I - Z^+ Z
+        assert np.max(np.abs(q - blk.q)) < 2e-6                  # Z^+ e_c
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+@pytest.mark.parametrize("K", [1, 7, 60])
+def test_fixed_iterations_parity(name, K, torch):
+    p = SMALL[name]()
+    o = O.Oracle(p)
+    ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=K)
+    s = gpu_solver([p], torch)
+    rc, st, phi, psi, lam, u, xn = run_fixed(s, torch, p.x0, K)
+    assert st[0]["iters"] == K
+    assert rel(psi, ref.Psi) <= REL
+    assert rel(lam, ref.Lam) <= REL or np.linalg.norm(ref.Lam) < 1e-6
+    assert rel(phi, ref.Phi) <= REL
+    u_ref = o.control(ref)
+    assert rel(u, u_ref) <= REL or np.max(np.abs(u - u_ref)) < 1e-7
+    xn_ref = o.dynamics(p.x0, u)  # dynamics of the GPU's own u, FP64
+    assert np.max(np.abs(xn.reshape(-1) - xn_ref.reshape(-1))) < 1e-6
+    s.close()
+
+
+def test_stopped_closed_loop_chain10(torch):
+    """20 closed-loop MPC steps of the N=10 chain; both sides solve from the
+    oracle's x(tau) at each step.  Cold and warm (previous-step) starts."""
+    import paper_2103_14990_gb300 as pkg
+    p = I.chain10()
+    o = O.Oracle(p)
+    for warm, wname in [(pkg.WARM_COLD, "cold"), (pkg.WARM_PREVIOUS, "previous")]:
+        xs, us, its, _ = o.run_mpc(p.mpc_steps, warm=wname)
+        s = gpu_solver([p], torch)
+        worst = 0.0
+        for tau in range(p.mpc_steps):
+            x = torch.tensor(xs[tau].astype(np.float32), device="cuda")
+            u = torch.zeros(p.n_sub, 1, device="cuda")
+            rc, st = s.step(x, u, None, warm=warm if tau > 0 else pkg.WARM_COLD)
+            assert st[0]["status"] == 0
+            assert abs(st[0]["iters"] - its[tau]) <= max(3, 0.02 * its[tau])
+            e = rel(u.cpu().numpy(), us[tau])
+            worst = max(worst, e)
+        assert worst <= 5 * REL, (wname, worst)
+        s.close()
+
+
+def test_batch_equals_single_instances(torch):
+    """Instances solved together in one persistent launch give bit-identical
+    results to the same instances solved alone."""
+    probs = [SMALL["chain10"](), SMALL["grid5x5_T6_d2_box"](), SMALL["chain16_T10_d3_box"]()]
+    sb = gpu_solver(probs, torch)
+    x0 = np.concatenate([p.x0 for p in probs])
+    rc, st, phi, psi, lam, u, xn = run_fixed(sb, torch, x0, 25)
+    off = 0
+    uoff = 0
+    for p in probs:
+        s1 = gpu_solver([p], torch)
+        r1 = run_fixed(s1, torch, p.x0, 25)
+        n = s1.info()["state_floats"]
+        assert np.array_equal(psi[off:off + n], r1[3])
+        assert np.array_equal(lam[off:off + n], r1[4])
+        assert np.array_equal(u[uoff:uoff + p.n_sub], r1[5])
+        off += n
+        uoff += p.n_sub
+        s1.close()
+    sb.close()
+
+
+def test_batch_stopping_per_instance(torch):
+    """Each instance of a batch stops at its own convergence iteration."""
+    import paper_2103_14990_gb300 as pkg
+    probs = [SMALL["chain10"](), SMALL["grid3x4_T4_d1"]()]
+    sb = gpu_solver(probs, torch)
+    x = torch.tensor(np.concatenate([p.x0 for p in probs]).astype(np.float32), device="cuda")
+    u = torch.zeros(sum(p.n_sub for p in probs), 1, device="cuda")
+    rc, st = sb.step(x, u, None, warm=pkg.WARM_COLD)
+    for p, s in zip(probs, st):
+        o = O.Oracle(p)
+        ref = O.admm(o.lay, o.blocks, p.x0)
+        assert s["status"] == 0
+        assert abs(s["iters"] - ref.iters) <= max(3, 0.02 * ref.iters)
+    sb.close()
+
+
+def test_host_buffer_step_matches_device_step(torch):
+    import paper_2103_14990_gb300 as pkg
+    p = SMALL["chain16_T10_d3_box"]()
+    s = gpu_solver([p], torch)
+    rc, u_h, xn_h, st_h = s.step_host(p.x0, warm=pkg.WARM_COLD)
+    x = torch.tensor(p.x0.astype(np.float32), device="cuda")
+    u = torch.zeros(p.n_sub, 1, device="cuda")
+    xn = torch.zeros_like(x)
+    rc2, st = s.step(x, u, xn, warm=pkg.WARM_COLD)
+    assert np.array_equal(u.cpu().numpy().reshape(-1), u_h)
+    assert np.array_equal(xn.cpu().numpy().reshape(-1), xn_h)
+    assert st[0]["iters"] == st_h[0]["iters"]
+    s.close()
+
+
+def test_max_iter_status(torch):
+    import paper_2103_14990_gb300 as pkg
+    p = SMALL["chain10"]()
+    p.max_iter = 3
+    s = gpu_solver([p], torch)
+    x = torch.tensor(p.x0.astype(np.float32), device="cuda")
+    u = torch.zeros(p.n_sub, 1, device="cuda")
+    rc, st = s.step(x, u, None, warm=pkg.WARM_COLD)
+    assert rc == pkg.DLMPC_MAX_ITER and st[0]["status"] == pkg.DLMPC_MAX_ITER and st[0]["iters"] == 3
+    s.close()
