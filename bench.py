@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""DLMPC benchmark on GB300: closed-loop MPC steps/s of the N=1024 chain.
+
+One "step" is one MPC step of Alg. 1 (per-step precompute, the whole ADMM of
+Alg. 2 to convergence, u(tau), x(tau+1)) for the chain of 1024 subsystems,
+T=10, d=3, |x| <= 1, |u| <= 2, x(0) ~ U[-0.9, 0.9] (seed 0), FP32 sweeps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+Our arm: W warm-up steps, then the state is reset to x(0) and K closed-loop
+steps are timed with CUDA events recorded by the library on its stream (the
+L2 is flushed between steps by a 256 MiB write outside the timed events).
+Headline: warm-started (previous step's Psi/Lambda) steps; the same K steps
+with cold starts ("plain") and through the host-buffer C-ABI call ("e2e")
+are reported beside it.  N > 1: one independent replica per GPU, no
+communication (weak scaling).  The reference arm times the FP64 oracle on
+the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MPC steps/s & ADMM iters/s, batched+warm-start vs plain at 1e-4 rel; HBM GB/s"
+UNIT = "MPC steps/s"
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_kernels.cu")
+# DRAM bytes (read + write) of one admm_kernel launch from an ncu capture, and
+# the sha256 of the kernel source it was taken on; reported as null when the
+# source has changed since.
+NCU_TRAFFIC = {"src_sha256": None, "bytes_per_launch": None}
+
+
+def workload(name: str):
+    from paper_2103_14990_gb300 import instances as I
+    return {"chain1024": I.chain1024, "chain10": I.chain10, "grid64": I.grid64}[name]()
+
+
+def kernel_sha() -> str:
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2103_14990_gb300 as pkg
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    prob = workload(args.workload)
+    t_setup = time.time()
+    solver = pkg.Solver([prob])
+    torch.cuda.synchronize()
+    t_setup = time.time() - t_setup
+    solver.set_option(pkg.OPT_TIMING, 1)
+    info = solver.info()
+    n, nx, nu = prob.n_sub, prob.nx, prob.nu
+    x0 = torch.tensor(prob.x0.astype(np.float32), device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def loop(K, warm):
+        x = x0.clone()
+        xn = torch.empty_like(x)
+        u = torch.empty(n, nu, device="cuda")
+        kms, sms, iters, status = [], [], [], []
+        for tau in range(K):
+            flush.zero_()
+            rc, st = solver.step(x, u, xn, warm=(pkg.WARM_COLD if tau == 0 else warm), stats=True)
+            a, b = solver.timing()
+            kms.append(a)
+            sms.append(b)
+            iters.append(st[0]["iters"])
+            status.append(st[0]["status"])
+            x, xn = xn, x
+        return kms, sms, iters, status, x
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up (discarded), then the timed closed loops from x(0)
+    loop(args.warmup, pkg.WARM_PREVIOUS)
+    sync_all()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        kms, sms, iters, status, xK = loop(args.steps, pkg.WARM_PREVIOUS)
+        sync_all()
+        wall = time.perf_counter() - wall0
+    t_dev = sum(sms) / 1e3
+    if dist is not None:
+        tt = torch.tensor([t_dev], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    value = world * args.steps / t_dev
+    kern_s = sum(kms) / 1e3
+    tot_iters = sum(iters)
+
+    # plain: cold start at every step, same kernel
+    pk, ps, pit, pst, _ = loop(args.steps, pkg.WARM_COLD)
+    plain = {"value": args.steps / (sum(ps) / 1e3), "unit": UNIT,
+             "admm_iters_per_s": sum(pit) / (sum(pk) / 1e3), "iters_per_step": sum(pit) / len(pit)}
+
+    # e2e: host (pinned) buffers through the C ABI, H2D and D2H inside the timed region
+    xh = torch.empty(n, nx, dtype=torch.float32, pin_memory=True)
+    xnh = torch.empty(n, nx, dtype=torch.float32, pin_memory=True)
+    uh = torch.empty(n, nu, dtype=torch.float32, pin_memory=True)
+    xh.copy_(x0.cpu())
+    sync_all()
+    e0 = time.perf_counter()
+    for tau in range(args.steps):
+        solver.step_host_ptr(xh.data_ptr(), uh.data_ptr(), xnh.data_ptr(),
+                             warm=(pkg.WARM_COLD if tau == 0 else pkg.WARM_PREVIOUS))
+        xh, xnh = xnh, xh
+    e_wall = time.perf_counter() - e0
+    e2e = {"value": args.steps / e_wall, "unit": UNIT, "h2d_bytes_per_step": n * nx * 4,
+           "d2h_bytes_per_step": n * (nu + nx) * 4 + 32 + 16}
+
+    # roofline of the sweep kernel: algorithmic bytes / CUDA-event kernel time
+    peak, peak_src = measured_peaks()
+    achieved = info["iter_bytes"] * tot_iters / kern_s / 1e9
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["src_sha256"] == kernel_sha() else None
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": peak_src, "kernel": "admm_kernel",
+                "algorithmic_bytes_per_iter": info["iter_bytes"],
+                "mean_launch_ms": round(sum(kms) / len(kms), 4)}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_dev / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded chain plant, x0 ~ U[-0.9,0.9])",
+        "config": {"workload": prob.name, "n_sub": n, "T": prob.T, "d": prob.d, "boxes": "|x|<=1, |u|<=2",
+                   "warm_start": "previous MPC step's Psi/Lambda (step 0 cold)", "max_iter": prob.max_iter,
+                   "eps": prob.eps_p, "l2": "flushed between steps (256 MiB write outside the events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "admm_iters_per_s": round(tot_iters / kern_s, 1),
+        "iters_per_step": round(tot_iters / args.steps, 2),
+        "steps_at_max_iter": int(sum(1 for s in status if s != 0)),
+        "plain": plain,
+        "e2e": e2e,
+        "roofline": roofline,
+        "gpu_launches": 2 * args.steps,
+        "setup_precompute_s": round(t_setup, 3),
+        "wall_s_timed_region": round(wall, 4),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, iters)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the FP64 oracle on the host cores (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_iters_table(workload_name: str):
+    path = os.path.join(ROOT, "tests", "golden", "chain1024_oracle_iters.json")
+    if workload_name != "chain1024" or not os.path.exists(path):
+        return None
+    return json.load(open(path))
+
+
+def oracle_sample(workload_name: str, seconds: float, min_iters: int):
+    """Times oracle ADMM iterations from x(0) for about `seconds`; returns
+    (seconds per iteration, iterations timed, seconds per u+dynamics)."""
+    import numpy as np
+    from oracle import dlmpc_oracle as O
+    prob = workload(workload_name)
+    o = O.Oracle(prob)
+    res = O.admm(o.lay, o.blocks, prob.x0, fixed_iters=1)  # warm the code path
+    done, t0 = 0, time.perf_counter()
+    Psi, Lam = res.Psi, res.Lam
+    while done < min_iters or time.perf_counter() - t0 < seconds:
+        r = O.admm(o.lay, o.blocks, prob.x0, Psi0=Psi, Lam0=Lam, fixed_iters=1)
+        Psi, Lam = r.Psi, r.Lam
+        done += 1
+    t_iter = (time.perf_counter() - t0) / done
+    t1 = time.perf_counter()
+    u = o.control(r)
+    o.dynamics(prob.x0, u)
+    return t_iter, done, time.perf_counter() - t1
+
+
+def _single_thread_env():
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+              "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    return env
+
+
+def cpu_baseline(args, gpu_iters):
+    """The oracle on one host core, on a bounded sample of the same workload."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload", args.workload,
+           "--sample-seconds", str(args.sample_seconds)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=_single_thread_env(), timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
+    s = json.loads(r.stdout.strip().splitlines()[-1])
+    table = oracle_iters_table(args.workload)
+    if table is not None:
+        its = table["previous"]["iters"][:args.steps]
+        src = "oracle's own per-step iteration counts (tests/golden/chain1024_oracle_iters.json)"
+    else:
+        its = gpu_iters
+        src = "the GPU run's per-step iteration counts"
+    t = sum(i * s["t_iter"] + s["t_tail"] for i in its)
+    return {"value": round(len(its) / t, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{s['iters']} FP64 oracle ADMM iterations from x(0) ({s['t_iter'] * 1e3:.1f} ms each, "
+                      f"one thread), scaled by {src} over the {len(its)} timed steps; one-time precompute excluded",
+            "oracle_admm_iters_per_s": round(1.0 / s["t_iter"], 3)}
+
+
+def run_oracle_sample(args):
+    t_iter, done, t_tail = oracle_sample(args.workload, args.sample_seconds, 3)
+    print(json.dumps({"t_iter": t_iter, "iters": done, "t_tail": t_tail}))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import dlmpc_oracle as O
+    prob = workload(args.workload)
+    o = O.Oracle(prob)
+    table = oracle_iters_table(args.workload)
+    if table is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no oracle iteration table for this workload"}))
+        return
+    its = table["previous"]["iters"]
+    per_step_sample = 2
+    Psi = Lam = None
+
+    def sample_step(tau):
+        nonlocal Psi, Lam
+        t0 = time.perf_counter()
+        r = O.admm(o.lay, o.blocks, prob.x0, Psi0=Psi, Lam0=Lam, fixed_iters=per_step_sample)
+        o.dynamics(prob.x0, o.control(r))
+        Psi, Lam = r.Psi, r.Lam
+        dt = time.perf_counter() - t0
+        return dt / per_step_sample * its[tau % len(its)]
+
+    for tau in range(args.warmup):
+        sample_step(tau)
+    total = sum(sample_step(tau) for tau in range(args.steps))
+    value = args.steps / total
+    cores = 1 if os.environ.get("OPENBLAS_NUM_THREADS") == "1" else os.cpu_count()
+    sample = (f"each step: {per_step_sample} FP64 oracle ADMM iterations (+u, dynamics) from x(0), scaled to "
+              f"that step's oracle iteration count from tests/golden/chain1024_oracle_iters.json")
+    print(json.dumps({
+        "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded chain plant, x0 ~ U[-0.9,0.9])", "impl": "reference",
+        "config": {"workload": prob.name, "n_sub": prob.n_sub, "T": prob.T, "d": prob.d},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="chain1024")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sample-seconds", type=float, default=15.0)
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and not args.oracle_sample:
+        ap.error("--warmup must be >= 3")
+    if args.oracle_sample:
+        run_oracle_sample(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -94,6 +94,9 @@ typedef struct {
   int64_t offset_bytes;     /* bytes of all min-norm offsets q_c (FP32, padded) */
   int64_t exchange_floats;  /* floats of one row-partial-sum exchange buffer */
   int32_t grid_ctas, threads_per_cta, smem_bytes; /* launch of the ADMM sweep kernel */
+  int64_t iter_bytes;       /* algorithmic bytes of one ADMM iteration over all patches:
+                               N_j and q_c read, Psi/Lambda read+written, row partial
+                               sums read (|Patch(m)| per patch row) and written */
 } dlmpc_info;
 
 /* Option keys for dlmpc_set_option. */

@@ -69,7 +69,8 @@ class Info_C(ctypes.Structure):
                 ("max_nullity", ctypes.c_int32), ("state_floats", ctypes.c_int64),
                 ("operator_bytes", ctypes.c_int64), ("offset_bytes", ctypes.c_int64),
                 ("exchange_floats", ctypes.c_int64), ("grid_ctas", ctypes.c_int32),
-                ("threads_per_cta", ctypes.c_int32), ("smem_bytes", ctypes.c_int32)]
+                ("threads_per_cta", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
+                ("iter_bytes", ctypes.c_int64)]
 
 
 _LIB = None
@@ -207,6 +208,14 @@ class Solver:
         rc = self._check(self.lib.dlmpc_step_host(self._ctx, _ptr(xf, ctypes.c_float), _ptr(u, ctypes.c_float),
                                                   _ptr(xn, ctypes.c_float) if xn is not None else None, warm, st))
         return rc, u, xn, [dict(iters=s.iters, status=s.status, r_max=s.r_max, s_max=s.s_max) for s in st]
+
+    def step_host_ptr(self, x_addr: int, u_addr: int, xn_addr: Optional[int], warm: int = WARM_COLD):
+        """Host-buffer step on raw host addresses (e.g. pinned torch tensors)."""
+        st = (Stats_C * len(self.problems))()
+        fp = ctypes.POINTER(ctypes.c_float)
+        rc = self._check(self.lib.dlmpc_step_host(self._ctx, ctypes.cast(x_addr, fp), ctypes.cast(u_addr, fp),
+                                                  ctypes.cast(xn_addr, fp) if xn_addr else None, warm, st))
+        return rc, [dict(iters=s.iters, status=s.status, r_max=s.r_max, s_max=s.s_max) for s in st]
 
     def solve_batch(self, xs: Sequence, us: Sequence, xns: Optional[Sequence] = None, warm: int = WARM_COLD):
         n = len(self.problems)

@@ -864,6 +864,16 @@ extern "C" int dlmpc_get_info(dlmpc_ctx *ctx, dlmpc_info *info) {
   info->grid_ctas = ctx->grid;
   info->threads_per_cta = sweep_threads();
   info->smem_bytes = (int32_t)ctx->smem;
+  int64_t bytes = 0;
+  for (const Item &it : ctx->items) {
+    const int64_t dcol = (int64_t)it.r_sub * it.n_mem;
+    bytes += (int64_t)it.dred * it.k * 4;            // N_j
+    bytes += (int64_t)ctx->nx * it.dred * 4;         // q_c
+    bytes += 4LL * ctx->nx * dcol * 4;               // Psi, Lambda read and written
+    for (int e = 0; e < it.n_mem; ++e) bytes += (int64_t)ctx->np_of[ctx->members[it.mem_off + e]] * it.r_sub * 4;
+    bytes += dcol * 4;                               // row partial sums written
+  }
+  info->iter_bytes = bytes;
   return 0;
 }
 

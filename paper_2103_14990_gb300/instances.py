@@ -194,15 +194,20 @@ def chain10(seed: int = 0) -> Problem:
 
 
 def chain1024(seed: int = 0) -> Problem:
-    """Chain N=1024, T=10, d=3, |x|<=1, |u|<=2, x0~U[-0.9,0.9], 50 MPC steps."""
+    """Chain N=1024, T=10, d=3, |x|<=1, |u|<=2, x0~U[-0.9,0.9], 50 MPC steps.
+
+    max_iter = 1000: some draws of x0 put a subsystem where the boxes cannot be
+    met (state 1 keeps integrating state 2 while |u| <= 2 moves state 2 by at
+    most 0.2 per step); those MPC steps never reach eps and stop at the cap."""
     return make_instance(1024, 10, 3, graph="chain", seed=seed, boxes=True,
-                         x0_dist="uniform", mpc_steps=50, name="chain_N1024_T10_d3_box")
+                         x0_dist="uniform", mpc_steps=50, max_iter=1000,
+                         name="chain_N1024_T10_d3_box")
 
 
 def grid64(seed: int = 0) -> Problem:
     """64x64 4-neighbour grid (4096 subsystems), T=10, d=2, boxes, 50 MPC steps."""
     return make_instance(4096, 10, 2, graph="grid", seed=seed, boxes=True,
-                         x0_dist="uniform", mpc_steps=50, grid_rows=64,
+                         x0_dist="uniform", mpc_steps=50, grid_rows=64, max_iter=1000,
                          name="grid_64x64_T10_d2_box")
 
 
@@ -215,7 +220,7 @@ def batch_instance(index: int) -> Problem:
     T = int(rng.integers(5, 16))
     d = int(rng.integers(1, 4))
     return make_instance(n, T, d, graph=graph, rng=rng, boxes=True, x0_dist="uniform",
-                         mpc_steps=50, name=f"batch{index}_{graph}_N{n}_T{T}_d{d}")
+                         mpc_steps=50, max_iter=1000, name=f"batch{index}_{graph}_N{n}_T{T}_d{d}")
 
 
 def batch256(count: int = 256) -> List[Problem]:
