@@ -169,6 +169,32 @@ int dlmpc_get_operator(dlmpc_ctx *ctx, int32_t j, double *N, int32_t n_cap,
  * Waits for the step to finish. */
 int dlmpc_get_timing(dlmpc_ctx *ctx, float *ms);
 
+/* Allocation-free re-factorisation of one patch constraint block.  The paper
+ * has no counterpart: it serves callers that must not allocate device memory
+ * once their control loop runs, such as a real-time MPC thread refreshing the
+ * patches touched by a model update between two steps (cudaMalloc may
+ * synchronise the whole device and its latency is unbounded), or code that is
+ * limited to a memory budget fixed at start-up.
+ * Computes in FP64 what dlmpc_precompute computes for one column patch: from
+ * the constraint block Z_dev (m x D, row-major) and nrhs right-hand sides
+ * rhs_dev (nrhs x m), an orthonormal null-space basis N_dev (D x k_cap,
+ * row-major; the first `nullity` columns are written, the others zeroed), the
+ * min-norm solutions q_dev (nrhs x D), rank_nullity_dev[2] = {rank, nullity}
+ * and feas_dev[0] = max_c ||Z q_c - rhs_c||_inf.  All pointers are device
+ * pointers owned by the caller; nothing is allocated.
+ * Workspace: one static device array of DLMPC_NOALLOC_MAX_DOUBLES doubles
+ * (8 MiB), held by every GPU that loads the library until the process exits.
+ * A block needing more than that (D*m + (3+nrhs)*m + 8*D + m/2 + 1 doubles)
+ * or nrhs > 32 returns DLMPC_ERR_ARG without launching anything.  The array's
+ * device address is looked up on the first call on each device, with that
+ * device current; make that first call before any stream capture.  Every call
+ * uses the same array: calls that overlap on the GPU race, so serialise them.
+ * Asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream). */
+#define DLMPC_NOALLOC_MAX_DOUBLES (1 << 20)
+int dlmpc_factor_patch_noalloc(const double *Z_dev, int32_t m, int32_t D, const double *rhs_dev,
+                               int32_t nrhs, double *N_dev, int32_t k_cap, double *q_dev,
+                               int32_t *rank_nullity_dev, double *feas_dev, void *stream);
+
 const char *dlmpc_last_error(dlmpc_ctx *ctx);
 void dlmpc_destroy(dlmpc_ctx *ctx);
 

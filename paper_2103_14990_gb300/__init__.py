@@ -42,6 +42,7 @@ EXPORTED = [
     "dlmpc_setup", "dlmpc_precompute", "dlmpc_step", "dlmpc_solve_batch", "dlmpc_step_host",
     "dlmpc_set_option", "dlmpc_get_info", "dlmpc_get_state", "dlmpc_set_state",
     "dlmpc_get_patch", "dlmpc_get_operator", "dlmpc_get_timing", "dlmpc_last_error", "dlmpc_destroy",
+    "dlmpc_factor_patch_noalloc",
 ]
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -103,6 +104,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dlmpc_last_error.restype = ctypes.c_char_p
     lib.dlmpc_destroy.argtypes = [vp]
     lib.dlmpc_destroy.restype = None
+    lib.dlmpc_factor_patch_noalloc.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_int32, vp,
+                                               ctypes.c_int32, vp, vp, vp, vp]
     _LIB = lib
     return lib
 
