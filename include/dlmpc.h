@@ -94,6 +94,9 @@ typedef struct {
   int64_t offset_bytes;     /* bytes of all min-norm offsets q_c (FP32, padded) */
   int64_t exchange_floats;  /* floats of one row-partial-sum exchange buffer */
   int32_t grid_ctas, threads_per_cta, smem_bytes; /* launch of the ADMM sweep kernel */
+  int32_t group_threads, groups_per_cta, wave; /* sweep shape (DLMPC_OPT_SWEEP_SHAPE) */
+  int32_t resident_n_items;     /* patches whose N_j stays in shared memory for the whole step */
+  int32_t resident_state_items; /* patches whose Psi, Lambda and q stay in shared memory */
   int64_t iter_bytes;       /* algorithmic bytes of one ADMM iteration over all patches:
                                N_j and q_c read, Psi/Lambda read+written, row partial
                                sums read (|Patch(m)| per patch row) and written */
@@ -104,9 +107,12 @@ typedef struct {
 #define DLMPC_OPT_MAX_ITER 2      /* overrides every instance's max_iter */
 #define DLMPC_OPT_TIMEOUT_MS 3    /* bound of every device-side wait (default 2000) */
 #define DLMPC_OPT_EXPORT_PHI 4    /* != 0: keep the last Phi for dlmpc_get_state */
-#define DLMPC_OPT_CTAS_PER_SM 5   /* ADMM sweep CTAs per SM (0 = occupancy maximum) */
-#define DLMPC_OPT_SMEM_BYTES 6    /* dynamic shared memory of the sweep kernel (0 = auto) */
+#define DLMPC_OPT_SWEEP_SHAPE 5   /* sweep launch: threads per group * 10000 + groups per CTA * 100
+                                     + Phi-step wave (e.g. 1280402); replans the launch */
 #define DLMPC_OPT_TIMING 7        /* != 0: record CUDA events around every step (dlmpc_get_timing) */
+#define DLMPC_OPT_TRACE 9         /* != 0: record phase timestamps of the sweep (dlmpc_get_trace) */
+#define DLMPC_OPT_RESIDENCY 8     /* shared-memory residency during a step: 0 none (all streamed),
+                                     1 Psi/Lambda/q, 2 (default) also N where it fits; replans */
 
 /* Builds the locality structure (hop-distance BFS, Patch(j), rows of Z_AB that
  * touch each patch) for n_inst instances, copies all inputs to the device and
@@ -162,6 +168,13 @@ int dlmpc_get_patch(dlmpc_ctx *ctx, int32_t j, int32_t *members, int32_t cap);
  * row-major, slot-0 state rows zero) and q (nx x D_col).  Returns k. */
 int dlmpc_get_operator(dlmpc_ctx *ctx, int32_t j, double *N, int32_t n_cap,
                        double *q, int32_t q_cap);
+
+/* Sweep phase timestamps of the last step (needs DLMPC_OPT_TRACE): for every
+ * CTA, the first 8 iterations, 8 %globaltimer stamps (ns) taken by thread 0:
+ * 0 iteration start, 1 first Phi-step wave done, 2 first patch projected,
+ * 3 last patch done, 4 all groups done, 5 grid barrier passed (0 = not taken).
+ * stamps: host [cap]; returns the number of CTAs.  Synchronous. */
+int dlmpc_get_trace(dlmpc_ctx *ctx, unsigned long long *stamps, int64_t cap);
 
 /* GPU time of the last step, from CUDA events recorded on the context's
  * stream (needs DLMPC_OPT_TIMING): ms[0] = the ADMM sweep kernel alone,

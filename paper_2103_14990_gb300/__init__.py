@@ -33,15 +33,17 @@ OPT_FIXED_ITERS = 1
 OPT_MAX_ITER = 2
 OPT_TIMEOUT_MS = 3
 OPT_EXPORT_PHI = 4
-OPT_CTAS_PER_SM = 5
-OPT_SMEM_BYTES = 6
+OPT_SWEEP_SHAPE = 5
 OPT_TIMING = 7
+OPT_RESIDENCY = 8
+OPT_TRACE = 9
 
 # Every entry point declared in include/dlmpc.h (checked by the tests).
 EXPORTED = [
     "dlmpc_setup", "dlmpc_precompute", "dlmpc_step", "dlmpc_solve_batch", "dlmpc_step_host",
     "dlmpc_set_option", "dlmpc_get_info", "dlmpc_get_state", "dlmpc_set_state",
-    "dlmpc_get_patch", "dlmpc_get_operator", "dlmpc_get_timing", "dlmpc_last_error", "dlmpc_destroy",
+    "dlmpc_get_patch", "dlmpc_get_operator", "dlmpc_get_timing", "dlmpc_get_trace", "dlmpc_last_error",
+    "dlmpc_destroy",
     "dlmpc_factor_patch_noalloc",
 ]
 
@@ -71,6 +73,8 @@ class Info_C(ctypes.Structure):
                 ("operator_bytes", ctypes.c_int64), ("offset_bytes", ctypes.c_int64),
                 ("exchange_floats", ctypes.c_int64), ("grid_ctas", ctypes.c_int32),
                 ("threads_per_cta", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
+                ("group_threads", ctypes.c_int32), ("groups_per_cta", ctypes.c_int32), ("wave", ctypes.c_int32),
+                ("resident_n_items", ctypes.c_int32), ("resident_state_items", ctypes.c_int32),
                 ("iter_bytes", ctypes.c_int64)]
 
 
@@ -100,6 +104,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dlmpc_get_patch.argtypes = [vp, ctypes.c_int32, _ip, ctypes.c_int32]
     lib.dlmpc_get_operator.argtypes = [vp, ctypes.c_int32, _dp, ctypes.c_int32, _dp, ctypes.c_int32]
     lib.dlmpc_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.dlmpc_get_trace.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int64]
     lib.dlmpc_last_error.argtypes = [vp]
     lib.dlmpc_last_error.restype = ctypes.c_char_p
     lib.dlmpc_destroy.argtypes = [vp]
@@ -235,6 +240,13 @@ class Solver:
         ms = (ctypes.c_float * 2)()
         self._check(self.lib.dlmpc_get_timing(self._ctx, ms))
         return float(ms[0]), float(ms[1])
+
+    def trace(self) -> np.ndarray:
+        """[ctas, 8 iterations, 8 points] globaltimer stamps (ns) of the last step."""
+        cap = 1 << 20
+        buf = np.zeros(cap, np.uint64)
+        n = self._check(self.lib.dlmpc_get_trace(self._ctx, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), cap))
+        return buf[:n * 64].reshape(n, 8, 8)
 
     def get_state(self, phi: bool = False):
         torch = self.torch

@@ -20,11 +20,9 @@ namespace dlmpc {
 cudaError_t launch_factor(const FactorParams &p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_repack(const Item *scratch_items, const Item *items, int n_items, const float *src, float *dst,
                           cudaStream_t s);
-const void *admm_kernel_ptr(int nx);
-int sweep_threads();
-size_t sweep_smem_bytes(int nx, int smem_n_floats, int max_dcol, int max_kpad);
-cudaError_t launch_admm(int nx, const Params &P, int max_dcol, int max_kpad, int grid, size_t smem,
-                        cudaStream_t s);
+const void *sweep_kernel_ptr(int nx, int gt);
+int sweep_group_floats(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad, int max_kpad, int max_nmem);
+cudaError_t launch_sweep(const Params &P, int gt, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_stats(const int32_t *inst_item_ptr, int n_inst, const float *item_r, const float *item_s,
                          const int32_t *inst_iters, const int32_t *err, int fixed, const float *epsp,
                          const float *epsd, dlmpc_stats *out, cudaStream_t s);
@@ -88,25 +86,29 @@ struct dlmpc_ctx {
   std::vector<int64_t> rhs_off;
   std::vector<int32_t> kub;
   bool precomputed = false;
-  int max_dcol = 0, max_kpad = 1;
+  int max_dcol = 0, max_kpad = 4, max_dred_pad = 4, max_nmem = 1;
   int64_t n_floats = 0, q_floats = 0;
-  // launch
-  int grid = 0, smem_n_floats = 0;
+  // launch plan of the sweep kernel
+  int grid = 0, gt = 128, ng = 4, wave = 2, grp_floats = 0, cta_floats = 0, max_local_inst = 1;
   size_t smem = 0;
-  std::vector<int32_t> cta_ptr, cta_items;
+  int64_t resident_n_items = 0, resident_state_items = 0;
+  int residency = 2;  // 0: nothing resident, 1: Psi/Lambda/q resident, 2: also N
+  int trace = 0;
+  std::vector<int32_t> grp_ptr, grp_items, cta_inst_ptr, cta_inst;
   // options
-  int fixed_iters = 0, max_iter_override = 0, export_phi = 0, ctas_per_sm = 0, smem_opt = 0;
+  int fixed_iters = 0, max_iter_override = 0, export_phi = 0;
   double timeout_ms = 2000.0;
   std::string err;
   // device
   DevBuf<Item> d_items;
-  DevBuf<int32_t> d_members, d_rev, d_np, d_cta_ptr, d_cta_items, d_adj_ptr, d_adj_idx, d_inst_iters, d_err,
-      d_inst_item_ptr, d_sub_off;
+  DevBuf<int32_t> d_members, d_rev, d_np, d_grp_ptr, d_grp_items, d_cta_inst_ptr, d_cta_inst, d_adj_ptr, d_adj_idx,
+      d_inst_iters, d_err, d_inst_item_ptr, d_sub_off;
   DevBuf<int64_t> d_goff;
   DevBuf<float> d_N, d_q, d_psi, d_lam, d_phi, d_G0, d_G1, d_S, d_qw, d_rw, d_xlo, d_xhi, d_ulo, d_uhi, d_rho,
       d_epsp, d_epsd, d_item_r, d_item_s, d_x, d_u, d_xn;
   DevBuf<double> d_Adiag, d_Aoff, d_B;
-  DevBuf<unsigned> d_bar, d_notconv;
+  DevBuf<unsigned long long> d_bar, d_trace;
+  DevBuf<unsigned> d_notconv;
   DevBuf<dlmpc_stats> d_stats;
   DevBuf<const float *> d_ptr_in;
   DevBuf<float *> d_ptr_out, d_ptr_out2;
@@ -415,6 +417,7 @@ extern "C" int dlmpc_setup(const dlmpc_problem *probs, int32_t n_inst, void *str
       it.k = 0;
       it.kpad = 1;
       ctx->max_dcol = std::max(ctx->max_dcol, r_sub * it.n_mem);
+      ctx->max_nmem = std::max(ctx->max_nmem, it.n_mem);
     }
   }
   ctx->state_floats = st_off;
@@ -487,8 +490,8 @@ int upload_static(dlmpc_ctx *ctx) {
   CK(ctx->d_S.alloc(ctx->n_sub), "alloc S");
   CK(ctx->d_item_r.alloc(ctx->n_sub), "alloc residuals");
   CK(ctx->d_item_s.alloc(ctx->n_sub), "alloc residuals");
-  CK(ctx->d_bar.alloc(1), "alloc barrier");
-  CK(ctx->d_notconv.alloc(3 * (ctx->n_inst + 1)), "alloc conv");
+  CK(ctx->d_bar.alloc(3), "alloc barrier");
+  CK(ctx->d_notconv.alloc(3 * ctx->n_inst), "alloc conv");
   CK(ctx->d_inst_iters.alloc(ctx->n_inst), "alloc iters");
   CK(ctx->d_err.alloc(8), "alloc err");
   CK(ctx->d_stats.alloc(ctx->n_inst), "alloc stats");
@@ -500,73 +503,154 @@ int upload_static(dlmpc_ctx *ctx) {
   return 0;
 }
 
-// Longest-processing-time assignment of column patches to CTAs.
-void assign_work(dlmpc_ctx *ctx, int grid) {
-  const int n = ctx->n_sub;
-  std::vector<double> cost(n);
-  for (int g = 0; g < n; ++g) {
-    const Item &it = ctx->items[g];
-    cost[g] = (double)it.dred * (2.0 * it.k + 4.0 * ctx->nx) + 8.0 * it.r_sub * it.n_mem + 2000.0;
-  }
-  std::vector<int> order(n);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+double item_cost(const dlmpc_ctx *ctx, const Item &it) {
+  return (double)it.dred * (2.0 * it.k + 4.0 * ctx->nx) + 8.0 * it.r_sub * it.n_mem + 2000.0;
+}
+
+// Longest-processing-time assignment of `ids` to `bins` bins.
+std::vector<std::vector<int32_t>> lpt(const dlmpc_ctx *ctx, const std::vector<int32_t> &ids, int bins) {
+  std::vector<int32_t> order = ids;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return item_cost(ctx, ctx->items[a]) > item_cost(ctx, ctx->items[b]);
+  });
   using P = std::pair<double, int>;
   std::priority_queue<P, std::vector<P>, std::greater<P>> heap;
-  for (int b = 0; b < grid; ++b) heap.push({0.0, b});
-  std::vector<std::vector<int32_t>> bins(grid);
+  for (int b = 0; b < bins; ++b) heap.push({0.0, b});
+  std::vector<std::vector<int32_t>> out(bins);
   for (int g : order) {
     auto top = heap.top();
     heap.pop();
-    bins[top.second].push_back(g);
-    heap.push({top.first + cost[g], top.second});
+    out[top.second].push_back(g);
+    heap.push({top.first + item_cost(ctx, ctx->items[g]), top.second});
   }
-  ctx->cta_ptr.assign(1, 0);
-  ctx->cta_items.clear();
-  for (auto &bn : bins) {
-    std::sort(bn.begin(), bn.end());
-    ctx->cta_items.insert(ctx->cta_items.end(), bn.begin(), bn.end());
-    ctx->cta_ptr.push_back((int32_t)ctx->cta_items.size());
-  }
+  return out;
 }
 
-int configure_launch(dlmpc_ctx *ctx) {
+// Plans the sweep launch for `gt` threads per group, `ng` groups per CTA and
+// Phi-step waves of `wave` items: one CTA per SM, items assigned to CTAs and
+// groups by longest processing time, then each CTA's shared-memory arena
+// filled with resident Psi/Lambda and q, then resident N, until it is full.
+int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = false) {
+  if (!(gt == 64 || gt == 128 || gt == 256) || ng < 1 || gt * ng > 1024 || wave < 1 || wave > 8)
+    return ctx->fail(DLMPC_ERR_ARG, "unsupported sweep shape");
+  if (ctx->max_kpad > 4 * gt) return ctx->fail(DLMPC_ERR_ARG, "null-space dimension too large for this group size");
+  const int nx = ctx->nx;
   int dev = 0, sms = 0, smem_optin = 0;
   CK(cudaGetDevice(&dev), "cudaGetDevice");
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
   CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-  int smem_sm = 0;
-  CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev), "attr");
-  int64_t full_n = 4;
-  for (const Item &it : ctx->items) full_n = std::max<int64_t>(full_n, (int64_t)it.dred_pad * it.kpad);
-  const size_t fixed = sweep_smem_bytes(ctx->nx, 0, ctx->max_dcol, ctx->max_kpad);
-  // Largest CTA count per SM that keeps every patch operator resident in
-  // shared memory; if none does, one CTA per SM streams N in row chunks.
-  int64_t best_n = 0;
-  const int want_c = ctx->ctas_per_sm;
-  for (int c = 8; c >= 1; --c) {
-    if (want_c > 0 && c != want_c) continue;
-    const int64_t per = std::min<int64_t>(smem_optin, (int64_t)smem_sm / c - 1024) - (int64_t)fixed;
-    if (per / 4 >= full_n) { best_n = full_n; break; }
-    if (c == 1 || want_c > 0) best_n = std::max<int64_t>(0, per / 4);
+  const void *fn = sweep_kernel_ptr(nx, gt);
+  if (!fn) return ctx->fail(DLMPC_ERR_ARG, "no sweep kernel for this nx / group size");
+  cudaFuncAttributes fa{};
+  CK(cudaFuncGetAttributes(&fa, fn), "cudaFuncGetAttributes");
+  const int64_t budget = ((int64_t)smem_optin - (int64_t)fa.sharedSizeBytes - 64) / 4;  // floats
+  const int n = ctx->n_sub;
+  // default: every SM busy, groups per CTA trimmed to the items per CTA;
+  // an explicit shape keeps its group count and trims the grid instead
+  const int grid = exact_groups ? std::max(1, std::min(sms, (n + ng - 1) / ng)) : std::max(1, std::min(sms, n));
+  if (!exact_groups) ng = std::max(1, std::min(ng, (n + grid - 1) / grid));
+  std::vector<int32_t> all(n);
+  std::iota(all.begin(), all.end(), 0);
+  auto ctas = lpt(ctx, all, grid);
+  int max_li = 1;
+  for (auto &ci : ctas) {
+    std::vector<int> insts;
+    for (int g : ci) insts.push_back(ctx->items[g].inst);
+    std::sort(insts.begin(), insts.end());
+    insts.erase(std::unique(insts.begin(), insts.end()), insts.end());
+    max_li = std::max<int>(max_li, (int)insts.size());
   }
-  if (best_n < 4 * ctx->max_kpad)
-    return ctx->fail(DLMPC_ERR_ARG, "patch operators too large for the shared-memory budget");
-  if (ctx->smem_opt > 0) best_n = std::min<int64_t>(best_n, (ctx->smem_opt - (int64_t)fixed) / 4);
-  best_n = std::max<int64_t>(best_n & ~int64_t(3), 4 * ctx->max_kpad);
-  best_n = std::min<int64_t>(best_n, round_up(full_n, 4));
-  ctx->smem_n_floats = (int)best_n;
-  ctx->smem = sweep_smem_bytes(ctx->nx, ctx->smem_n_floats, ctx->max_dcol, ctx->max_kpad);
-  const void *fn = admm_kernel_ptr(ctx->nx);
+  int64_t max_n = 4;
+  for (const Item &it : ctx->items) max_n = std::max<int64_t>(max_n, (int64_t)it.dred_pad * it.kpad);
+  const int cta_floats = 8 + 4 * ((2 * max_li + 3) / 4);
+  (void)max_n;  // N that is not resident is read from global memory directly
+  int64_t used_max = 0;
+  std::vector<std::vector<std::vector<int32_t>>> groups(grid);
+  for (int pass = 0; pass < 2; ++pass) {
+    const int grp = sweep_group_floats(nx, ctx->nu, gt, wave, ctx->max_dcol, ctx->max_dred_pad, ctx->max_kpad,
+                                       ctx->max_nmem);
+    const int64_t arena_cap = budget - (int64_t)ng * grp - cta_floats;
+    if (arena_cap < 0) return ctx->fail(DLMPC_ERR_ARG, "shared-memory budget exceeded by the group buffers");
+    used_max = 0;
+    ctx->resident_n_items = ctx->resident_state_items = 0;
+    bool any_streamed = false;
+    for (int b = 0; b < grid; ++b) {
+      groups[b] = lpt(ctx, ctas[b], ng);
+      int64_t used = 0;
+      // resident Psi/Lambda and q first (round robin over groups)
+      std::vector<int32_t> rr;
+      size_t depth = 0;
+      for (bool more = true; more; ++depth) {
+        more = false;
+        for (auto &gl : groups[b])
+          if (depth < gl.size()) { rr.push_back(gl[depth]); more = true; }
+      }
+      for (int id : rr) {
+        Item &it = ctx->items[id];
+        const int64_t need = 2LL * nx * it.r_sub * it.n_mem + (int64_t)nx * it.dred_pad;
+        it.n_sm = it.q_sm = it.st_sm = -1;
+        if (ctx->residency >= 1 && used + need <= arena_cap) {
+          it.st_sm = (int32_t)used;
+          it.q_sm = (int32_t)(used + 2LL * nx * it.r_sub * it.n_mem);
+          used += need;
+          ++ctx->resident_state_items;
+        }
+      }
+      for (int id : rr) {
+        Item &it = ctx->items[id];
+        const int64_t need = (int64_t)it.dred_pad * it.kpad;
+        if (ctx->residency >= 2 && used + need <= arena_cap) {
+          it.n_sm = (int32_t)used;
+          used += need;
+          ++ctx->resident_n_items;
+        } else {
+          any_streamed = true;
+        }
+      }
+      used_max = std::max(used_max, used);
+      // resident-N items first within each group
+      for (auto &gl : groups[b])
+        std::stable_partition(gl.begin(), gl.end(), [&](int id) { return ctx->items[id].n_sm >= 0; });
+    }
+    (void)any_streamed;
+    ctx->grp_floats = grp;
+    break;
+  }
+  ctx->grid = grid;
+  ctx->gt = gt;
+  ctx->ng = ng;
+  ctx->wave = wave;
+  ctx->cta_floats = cta_floats;
+  ctx->max_local_inst = max_li;
+  ctx->grp_ptr.assign(1, 0);
+  ctx->grp_items.clear();
+  ctx->cta_inst_ptr.assign(1, 0);
+  ctx->cta_inst.clear();
+  for (int b = 0; b < grid; ++b) {
+    std::vector<int> insts;
+    for (int g : ctas[b]) insts.push_back(ctx->items[g].inst);
+    std::sort(insts.begin(), insts.end());
+    insts.erase(std::unique(insts.begin(), insts.end()), insts.end());
+    for (int g : ctas[b])
+      ctx->items[g].lslot = int(std::lower_bound(insts.begin(), insts.end(), ctx->items[g].inst) - insts.begin());
+    ctx->cta_inst.insert(ctx->cta_inst.end(), insts.begin(), insts.end());
+    ctx->cta_inst_ptr.push_back((int32_t)ctx->cta_inst.size());
+    for (auto &gl : groups[b]) {
+      ctx->grp_items.insert(ctx->grp_items.end(), gl.begin(), gl.end());
+      ctx->grp_ptr.push_back((int32_t)ctx->grp_items.size());
+    }
+  }
+  ctx->smem = (size_t)((int64_t)ng * ctx->grp_floats + cta_floats + used_max) * 4;
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem), "smem attr");
   int occ = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sweep_threads(), ctx->smem), "occupancy");
-  if (occ < 1) return ctx->fail(DLMPC_ERR_ARG, "sweep kernel cannot be resident");
-  if (want_c > 0) occ = std::min(occ, want_c);
-  ctx->grid = std::min(ctx->n_sub, sms * occ);
-  assign_work(ctx, ctx->grid);
-  CK(upload(ctx->d_cta_ptr, ctx->cta_ptr, ctx->stream), "upload cta_ptr");
-  CK(upload(ctx->d_cta_items, ctx->cta_items, ctx->stream), "upload cta_items");
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, gt * ng, ctx->smem), "occupancy");
+  if (occ < 1 || grid > occ * sms) return ctx->fail(DLMPC_ERR_ARG, "sweep kernel cannot be co-resident");
+  cudaStream_t s = ctx->stream;
+  CK(upload(ctx->d_items, ctx->items, s), "upload items");
+  CK(upload(ctx->d_grp_ptr, ctx->grp_ptr, s), "upload plan");
+  CK(upload(ctx->d_grp_items, ctx->grp_items, s), "upload plan");
+  CK(upload(ctx->d_cta_inst_ptr, ctx->cta_inst_ptr, s), "upload plan");
+  CK(upload(ctx->d_cta_inst, ctx->cta_inst, s), "upload plan");
   return 0;
 }
 
@@ -646,7 +730,7 @@ extern "C" int dlmpc_precompute(dlmpc_ctx *ctx) {
       return ctx->fail(DLMPC_ERR_INFEASIBLE_LOCALITY, buf);
     }
     if (nul[g] > ctx->kub[g]) return ctx->fail(DLMPC_ERR_ARG, "null-space dimension above its structural bound");
-    if (nul[g] > 2 * sweep_threads()) return ctx->fail(DLMPC_ERR_ARG, "null-space dimension above 512");
+    if (nul[g] > 1000) return ctx->fail(DLMPC_ERR_ARG, "null-space dimension above 1000");
   }
   // packed layout: odd stride kpad, 16-byte aligned items
   int64_t noff = 0;
@@ -654,17 +738,28 @@ extern "C" int dlmpc_precompute(dlmpc_ctx *ctx) {
   for (int g = 0; g < ctx->n_sub; ++g) {
     Item &it = ctx->items[g];
     it.k = nul[g];
-    it.kpad = (it.k % 2 == 1) ? it.k : it.k + 1;
+    // row stride: multiple of 4 floats (16-byte vector loads) with an odd
+    // number of 16-byte units, so consecutive rows hit distinct bank groups
+    it.kpad = (int)round_up(std::max(it.k, 1), 4);
+    if ((it.kpad / 4) % 2 == 0) it.kpad += 4;
     it.n_off = noff;
     noff += round_up((int64_t)it.dred_pad * it.kpad, 4);
     ctx->max_kpad = std::max(ctx->max_kpad, it.kpad);
+    ctx->max_dred_pad = std::max(ctx->max_dred_pad, it.dred_pad);
   }
   ctx->n_floats = noff;
   CK(upload(ctx->d_items, ctx->items, s), "upload items");
   CK(ctx->d_N.alloc(noff), "alloc N");
   CK(launch_repack(d_scr.p, ctx->d_items.p, ctx->n_sub, d_Nscr.p, ctx->d_N.p, s), "repack_kernel");
   CK(cudaStreamSynchronize(s), "repack");
-  rc = configure_launch(ctx);
+  // default launch shape: the first that fits the shared-memory budget
+  static const int kShapes[][3] = {{128, 8, 1}, {128, 6, 1}, {128, 4, 2}, {128, 4, 1}, {128, 2, 1},
+                                   {256, 2, 1}, {128, 1, 1}, {256, 1, 1}, {64, 1, 1}};
+  rc = DLMPC_ERR_ARG;
+  for (const auto &sh : kShapes) {
+    rc = plan_sweep(ctx, sh[0], sh[1], sh[2]);
+    if (rc == 0) break;
+  }
   if (rc) return rc;
   CK(cudaStreamSynchronize(s), "precompute");
   ctx->precomputed = true;
@@ -688,13 +783,15 @@ int run_step(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_dev, in
       if (!e) CK(cudaEventCreate(&e), "cudaEventCreate");
     CK(cudaEventRecord(ctx->ev[0], s), "event");
   }
-  CK(cudaMemsetAsync(ctx->d_bar.p, 0, 4, s), "memset");
+  CK(cudaMemsetAsync(ctx->d_bar.p, 0, 3 * sizeof(unsigned long long), s), "memset");
   CK(cudaMemsetAsync(ctx->d_err.p, 0, 32, s), "memset");
   Params P{};
   P.items = ctx->d_items.p;
   P.n_items = ctx->n_sub;
-  P.cta_ptr = ctx->d_cta_ptr.p;
-  P.cta_items = ctx->d_cta_items.p;
+  P.grp_ptr = ctx->d_grp_ptr.p;
+  P.grp_items = ctx->d_grp_items.p;
+  P.cta_inst_ptr = ctx->d_cta_inst_ptr.p;
+  P.cta_inst = ctx->d_cta_inst.p;
   P.members = ctx->d_members.p;
   P.rev_slot = ctx->d_rev.p;
   P.np_of = ctx->d_np.p;
@@ -739,9 +836,24 @@ int run_step(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_dev, in
   P.nx = ctx->nx;
   P.nu = ctx->nu;
   P.timeout_ns = (unsigned long long)(ctx->timeout_ms * 1e6);
-  P.smem_n_floats = ctx->smem_n_floats;
+  P.ng = ctx->ng;
+  P.wave = ctx->wave;
+  P.max_nmem = ctx->max_nmem;
+  P.max_dcol = ctx->max_dcol;
+  P.max_dred_pad = ctx->max_dred_pad;
+  P.max_kpad = ctx->max_kpad;
+  P.grp_floats = ctx->grp_floats;
+  P.cta_floats = ctx->cta_floats;
+  P.max_local_inst = ctx->max_local_inst;
+  P.trace = nullptr;
+  if (ctx->trace) {
+    const size_t n = (size_t)ctx->grid * kTraceIters * kTracePoints;
+    if (ctx->d_trace.n != n) CK(ctx->d_trace.alloc(n), "alloc trace");
+    CK(cudaMemsetAsync(ctx->d_trace.p, 0, n * 8, s), "memset");
+    P.trace = ctx->d_trace.p;
+  }
   if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s), "event");
-  CK(launch_admm(ctx->nx, P, ctx->max_dcol, ctx->max_kpad, ctx->grid, ctx->smem, s), "admm_kernel launch");
+  CK(launch_sweep(P, ctx->gt, ctx->grid, ctx->smem, s), "sweep_kernel launch");
   if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s), "event");
   if (!stats) {
     if (ctx->timing) {
@@ -835,12 +947,18 @@ extern "C" int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value) {
       return 0;
     case DLMPC_OPT_EXPORT_PHI: ctx->export_phi = value != 0; return 0;
     case DLMPC_OPT_TIMING: ctx->timing = value != 0; return 0;
-    case DLMPC_OPT_CTAS_PER_SM:
-    case DLMPC_OPT_SMEM_BYTES: {
-      if (key == DLMPC_OPT_CTAS_PER_SM) ctx->ctas_per_sm = (int)value;
-      else ctx->smem_opt = (int)value;
-      if (ctx->precomputed) return configure_launch(ctx);
-      return 0;
+    case DLMPC_OPT_TRACE: ctx->trace = value != 0; return 0;
+    case DLMPC_OPT_RESIDENCY: {
+      if (!(value >= 0 && value <= 2)) return ctx->fail(DLMPC_ERR_ARG, "residency must be 0, 1 or 2");
+      ctx->residency = (int)value;
+      if (!ctx->precomputed) return 0;
+      return plan_sweep(ctx, ctx->gt, ctx->ng, ctx->wave, true);
+    }
+    case DLMPC_OPT_SWEEP_SHAPE: {
+      // value = gt * 10000 + ng * 100 + wave
+      const int v = (int)value;
+      if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "set the sweep shape after dlmpc_precompute");
+      return plan_sweep(ctx, v / 10000, (v / 100) % 100, v % 100, true);
     }
   }
   return ctx->fail(DLMPC_ERR_ARG, "unknown option");
@@ -862,8 +980,13 @@ extern "C" int dlmpc_get_info(dlmpc_ctx *ctx, dlmpc_info *info) {
   info->offset_bytes = ctx->q_floats * 4;
   info->exchange_floats = ctx->g_floats;
   info->grid_ctas = ctx->grid;
-  info->threads_per_cta = sweep_threads();
+  info->threads_per_cta = ctx->gt * ctx->ng;
   info->smem_bytes = (int32_t)ctx->smem;
+  info->group_threads = ctx->gt;
+  info->groups_per_cta = ctx->ng;
+  info->wave = ctx->wave;
+  info->resident_n_items = (int32_t)ctx->resident_n_items;
+  info->resident_state_items = (int32_t)ctx->resident_state_items;
   int64_t bytes = 0;
   for (const Item &it : ctx->items) {
     const int64_t dcol = (int64_t)it.r_sub * it.n_mem;
@@ -934,6 +1057,16 @@ extern "C" int dlmpc_get_operator(dlmpc_ctx *ctx, int32_t j, double *N, int32_t 
     }
   }
   return it.k;
+}
+
+extern "C" int dlmpc_get_trace(dlmpc_ctx *ctx, unsigned long long *stamps, int64_t cap) {
+  if (!ctx || !stamps) return DLMPC_ERR_ARG;
+  if (!ctx->d_trace.p) return ctx->fail(DLMPC_ERR_ARG, "no trace recorded (DLMPC_OPT_TRACE)");
+  const int64_t n = (int64_t)ctx->d_trace.n;
+  if (cap < n) return ctx->fail(DLMPC_ERR_ARG, "capacity too small");
+  CK(cudaMemcpyAsync(stamps, ctx->d_trace.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream), "D2H trace");
+  CK(cudaStreamSynchronize(ctx->stream), "trace");
+  return (int)(n / (kTraceIters * kTracePoints));
 }
 
 extern "C" int dlmpc_get_timing(dlmpc_ctx *ctx, float *ms) {

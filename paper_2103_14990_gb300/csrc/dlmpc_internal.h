@@ -27,13 +27,21 @@ struct Item {
   int64_t st_off;     // float offset of the column-owned state: nx x (r_sub * n_mem)
   int64_t z_off;      // offset into the reduced constraint CSR row pointer array
   int64_t ws_off;     // double offset of the factorisation workspace
+  // placement inside the sweep kernel's shared-memory arena of its CTA
+  int32_t n_sm;       // resident N (float offset), or -1: streamed through the group buffer
+  int32_t q_sm;       // resident q (float offset), or -1: read from global memory
+  int32_t st_sm;      // resident Psi then Lambda (2 * nx * D_col floats), or -1: global memory
+  int32_t lslot;      // slot of the item's instance among the instances of its CTA
 };
 
+// Arguments of the persistent ADMM sweep kernel.
 struct Params {
   const Item *items;
   int32_t n_items;
-  const int32_t *cta_ptr;     // [grid+1] items of CTA b: cta_items[cta_ptr[b] .. cta_ptr[b+1])
-  const int32_t *cta_items;
+  const int32_t *grp_ptr;     // [grid * ng + 1]: items of group g of CTA b are
+  const int32_t *grp_items;   //   grp_items[grp_ptr[b * ng + g] .. grp_ptr[b * ng + g + 1])
+  const int32_t *cta_inst_ptr;// [grid + 1]: instances touched by CTA b (local slot order)
+  const int32_t *cta_inst;
   const int32_t *members;     // global subsystem ids of every patch, per item at mem_off
   const int32_t *rev_slot;    // slot of the item's subsystem within Patch(member)
   const int32_t *np_of;       // |Patch(i)| per global subsystem
@@ -61,8 +69,8 @@ struct Params {
   const double *Bm;           // [sub][nx][nu]
   int32_t n_inst;
   const float *rho_i, *epsp_i, *epsd_i;  // per instance
-  unsigned int *bar;          // grid barrier counter
-  unsigned int *notconv;      // [3][n_inst+1]
+  unsigned long long *bar;    // [3] barrier counters: arrivals (low 32 bits) + not-converged items (high 32)
+  unsigned int *notconv;      // [3][n_inst] not-converged items per instance (used when n_inst > 1)
   int32_t *inst_iters;        // [n_inst]
   float *item_r, *item_s;     // [n_items]
   int32_t *err;               // [8]: code, cta, iteration, aux, iterations run
@@ -71,8 +79,18 @@ struct Params {
   int32_t warm;               // 0 cold, 1 previous
   int32_t nx, nu;
   unsigned long long timeout_ns;
-  int32_t smem_n_floats;      // floats of shared memory reserved for N chunks
+  // launch shape and shared-memory arena (floats)
+  int32_t ng;                 // thread groups per CTA
+  int32_t wave;               // items whose Phi-step is batched per group
+  int32_t max_dcol, max_dred_pad, max_kpad, max_nmem;
+  int32_t grp_floats;         // floats per group region
+  int32_t cta_floats;         // floats of the per-CTA counters (after the group regions)
+  int32_t max_local_inst;
+  unsigned long long *trace;  // optional [grid][kTraceIters][kTracePoints] globaltimer stamps
 };
+
+constexpr int kTraceIters = 8;
+constexpr int kTracePoints = 8;
 
 // Reduced constraint system of one item for the one-time factorisation:
 // CSR over the kept rows of Z_j restricted to the non-slot-0 variables, and

@@ -180,3 +180,36 @@ def test_max_iter_status(torch):
     rc, st = s.step(x, u, None, warm=pkg.WARM_COLD)
     assert rc == pkg.DLMPC_MAX_ITER and st[0]["status"] == pkg.DLMPC_MAX_ITER and st[0]["iters"] == 3
     s.close()
+
+
+SHAPES = [(128, 4, 2, 2), (128, 4, 1, 0), (64, 8, 3, 1), (256, 2, 2, 0), (128, 1, 1, 2), (64, 2, 4, 0)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("name", ["chain16_T10_d3_box", "grid5x5_T6_d2_box", "chain1_T2"])
+def test_sweep_shapes_and_streaming(name, shape, torch):
+    """Every launch shape (threads per group, groups per CTA, Phi-step wave)
+    and residency level (0: N, Psi, Lambda, q all streamed from global memory)
+    gives the same iterates as the oracle."""
+    import paper_2103_14990_gb300 as pkg
+    gt, ng, wave, res = shape
+    p = SMALL[name]()
+    o = O.Oracle(p)
+    K = 23
+    ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=K)
+    s = gpu_solver([p], torch)
+    s.set_option(pkg.OPT_RESIDENCY, res)
+    s.set_option(pkg.OPT_SWEEP_SHAPE, gt * 10000 + ng * 100 + wave)
+    info = s.info()
+    assert info["group_threads"] == gt and info["groups_per_cta"] == ng and info["wave"] == wave
+    if res == 0:
+        assert info["resident_n_items"] == 0 and info["resident_state_items"] == 0
+    rc, st, phi, psi, lam, u, xn = run_fixed(s, torch, p.x0, K)
+    assert rel(psi, ref.Psi) <= REL
+    assert rel(phi, ref.Phi) <= REL
+    assert rel(u, o.control(ref)) <= REL or np.max(np.abs(u - o.control(ref))) < 1e-7
+    # warm continuation from the state left behind (resident state written back)
+    rc, st2, phi2, psi2, lam2, u2, xn2 = run_fixed(s, torch, p.x0, K, warm=pkg.WARM_PREVIOUS)
+    ref2 = O.admm(o.lay, o.blocks, p.x0, Psi0=ref.Psi, Lam0=ref.Lam, fixed_iters=K)
+    assert rel(psi2, ref2.Psi) <= REL
+    s.close()
