@@ -34,8 +34,8 @@ sys.path.insert(0, ROOT)
 METRIC = "MPC steps/s & ADMM iters/s, batched+warm-start vs plain at 1e-4 rel; HBM GB/s"
 UNIT = "MPC steps/s"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_kernels.cu")
-# DRAM bytes (read + write) of one admm_kernel launch from an ncu capture, and
+KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_sweep.cu")
+# DRAM bytes (read + write) of one sweep_kernel launch from an ncu capture, and
 # the sha256 of the kernel source it was taken on; reported as null when the
 # source has changed since.
 NCU_TRAFFIC = {"src_sha256": None, "bytes_per_launch": None}
@@ -137,10 +137,15 @@ def run_ours(args):
     solver = pkg.Solver([prob])
     torch.cuda.synchronize()
     t_setup = time.time() - t_setup
-    solver.set_option(pkg.OPT_TIMING, 1)
-    info = solver.info()
     n, nx, nu = prob.n_sub, prob.nx, prob.nu
     x0 = torch.tensor(prob.x0.astype(np.float32), device="cuda")
+    tune = []
+    if not args.no_autotune:
+        t_tune = time.time()
+        tune = solver.autotune(x0, iters=args.tune_iters)
+        t_tune = time.time() - t_tune
+    solver.set_option(pkg.OPT_TIMING, 1)
+    info = solver.info()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def loop(K, warm):
@@ -181,6 +186,13 @@ def run_ours(args):
     kern_s = sum(kms) / 1e3
     tot_iters = sum(iters)
 
+    # the same closed loop replayed from captured CUDA graphs (whole-step events)
+    solver.set_option(pkg.OPT_GRAPH, 1)
+    loop(2, pkg.WARM_PREVIOUS)
+    gk, gs, git, gst, _ = loop(args.steps, pkg.WARM_PREVIOUS)
+    solver.set_option(pkg.OPT_GRAPH, 0)
+    graph = {"value": args.steps / (sum(gs) / 1e3), "unit": UNIT, "iters_per_step": sum(git) / len(git)}
+
     # plain: cold start at every step, same kernel
     pk, ps, pit, pst, _ = loop(args.steps, pkg.WARM_COLD)
     plain = {"value": args.steps / (sum(ps) / 1e3), "unit": UNIT,
@@ -207,7 +219,7 @@ def run_ours(args):
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["src_sha256"] == kernel_sha() else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": peak_src, "kernel": "admm_kernel",
+                "peak_source": peak_src, "kernel": "sweep_kernel",
                 "algorithmic_bytes_per_iter": info["iter_bytes"],
                 "mean_launch_ms": round(sum(kms) / len(kms), 4)}
 
@@ -226,6 +238,12 @@ def run_ours(args):
         "plain": plain,
         "e2e": e2e,
         "roofline": roofline,
+        "graph": graph,
+        "sweep": {"group_threads": info["group_threads"], "groups_per_cta": info["groups_per_cta"],
+                  "wave": info["wave"], "grid_ctas": info["grid_ctas"], "smem_bytes": info["smem_bytes"],
+                  "resident_n_items": info["resident_n_items"],
+                  "resident_state_items": info["resident_state_items"],
+                  "autotuned_shapes": len(tune), "autotune_s": round(t_tune, 3) if tune else None},
         "gpu_launches": 2 * args.steps,
         "setup_precompute_s": round(t_setup, 3),
         "wall_s_timed_region": round(wall, 4),
@@ -358,6 +376,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="chain1024")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune-iters", type=int, default=20)
     ap.add_argument("--sample-seconds", type=float, default=15.0)
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -111,6 +111,9 @@ typedef struct {
                                      + Phi-step wave (e.g. 1280402); replans the launch */
 #define DLMPC_OPT_TIMING 7        /* != 0: record CUDA events around every step (dlmpc_get_timing) */
 #define DLMPC_OPT_TRACE 9         /* != 0: record phase timestamps of the sweep (dlmpc_get_trace) */
+#define DLMPC_OPT_GRAPH 10        /* != 0: run each step as a CUDA graph (captured on first use for
+                                     a given set of buffers and options, then replayed); with it,
+                                     dlmpc_get_timing reports the whole step in both fields */
 #define DLMPC_OPT_RESIDENCY 8     /* shared-memory residency during a step: 0 none (all streamed),
                                      1 Psi/Lambda/q, 2 (default) also N where it fits; replans */
 
@@ -207,6 +210,22 @@ int dlmpc_get_timing(dlmpc_ctx *ctx, float *ms);
 int dlmpc_factor_patch_noalloc(const double *Z_dev, int32_t m, int32_t D, const double *rhs_dev,
                                int32_t nrhs, double *N_dev, int32_t k_cap, double *q_dev,
                                int32_t *rank_nullity_dev, double *feas_dev, void *stream);
+
+/* One measured launch shape of the sweep kernel. */
+typedef struct {
+  int32_t group_threads, groups_per_cta, wave, residency;
+  float ms;                 /* best sweep-kernel time of `iters` iterations */
+} dlmpc_tune_entry;
+
+/* Autotuner of the sweep launch (A7): for every feasible combination of
+ * threads per group, groups per CTA, Phi-step wave and shared-memory
+ * residency, runs `iters` fixed ADMM iterations from a cold start on x_dev
+ * (device, [n_sub_total][nx]), times the kernel with CUDA events, keeps the
+ * fastest plan and caches it per problem signature for the process.
+ * iters <= 0 applies the cached choice without measuring.  Psi and Lambda are
+ * restored afterwards.  entries (host, may be NULL) receives up to `cap`
+ * measured shapes.  Returns the number measured, or an error.  Synchronous. */
+int dlmpc_autotune(dlmpc_ctx *ctx, const float *x_dev, int32_t iters, dlmpc_tune_entry *entries, int32_t cap);
 
 const char *dlmpc_last_error(dlmpc_ctx *ctx);
 void dlmpc_destroy(dlmpc_ctx *ctx);

@@ -37,13 +37,14 @@ OPT_SWEEP_SHAPE = 5
 OPT_TIMING = 7
 OPT_RESIDENCY = 8
 OPT_TRACE = 9
+OPT_GRAPH = 10
 
 # Every entry point declared in include/dlmpc.h (checked by the tests).
 EXPORTED = [
     "dlmpc_setup", "dlmpc_precompute", "dlmpc_step", "dlmpc_solve_batch", "dlmpc_step_host",
     "dlmpc_set_option", "dlmpc_get_info", "dlmpc_get_state", "dlmpc_set_state",
     "dlmpc_get_patch", "dlmpc_get_operator", "dlmpc_get_timing", "dlmpc_get_trace", "dlmpc_last_error",
-    "dlmpc_destroy",
+    "dlmpc_destroy", "dlmpc_autotune",
     "dlmpc_factor_patch_noalloc",
 ]
 
@@ -64,6 +65,11 @@ class Problem_C(ctypes.Structure):
 class Stats_C(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("r_max", ctypes.c_float), ("s_max", ctypes.c_float)]
+
+
+class TuneEntry_C(ctypes.Structure):
+    _fields_ = [("group_threads", ctypes.c_int32), ("groups_per_cta", ctypes.c_int32), ("wave", ctypes.c_int32),
+                ("residency", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class Info_C(ctypes.Structure):
@@ -104,6 +110,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dlmpc_get_patch.argtypes = [vp, ctypes.c_int32, _ip, ctypes.c_int32]
     lib.dlmpc_get_operator.argtypes = [vp, ctypes.c_int32, _dp, ctypes.c_int32, _dp, ctypes.c_int32]
     lib.dlmpc_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.dlmpc_autotune.argtypes = [vp, vp, ctypes.c_int32, ctypes.POINTER(TuneEntry_C), ctypes.c_int32]
     lib.dlmpc_get_trace.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int64]
     lib.dlmpc_last_error.argtypes = [vp]
     lib.dlmpc_last_error.restype = ctypes.c_char_p
@@ -240,6 +247,15 @@ class Solver:
         ms = (ctypes.c_float * 2)()
         self._check(self.lib.dlmpc_get_timing(self._ctx, ms))
         return float(ms[0]), float(ms[1])
+
+    def autotune(self, x, iters: int = 20):
+        """Times every feasible sweep launch shape on `x` (CUDA tensor) and keeps
+        the fastest; returns the measured table (fastest first)."""
+        cap = 512
+        arr = (TuneEntry_C * cap)()
+        n = self._check(self.lib.dlmpc_autotune(self._ctx, ctypes.c_void_p(x.data_ptr()), iters, arr, cap))
+        out = [{f: getattr(arr[i], f) for f, _ in TuneEntry_C._fields_} for i in range(min(n, cap))]
+        return sorted(out, key=lambda e: e["ms"])
 
     def trace(self) -> np.ndarray:
         """[ctas, 8 iterations, 8 points] globaltimer stamps (ns) of the last step."""

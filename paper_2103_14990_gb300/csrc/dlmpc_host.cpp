@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <tuple>
 #include <limits>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <queue>
 #include <string>
@@ -116,6 +119,27 @@ struct dlmpc_ctx {
   int32_t *h_err = nullptr;        // pinned [8]
   int timing = 0;
   bool timed_step = false;
+  bool kernel_events = false;
+  int use_graph = 0;
+  int plan_version = 0;
+  struct GraphKey {
+    const float *x;
+    float *u, *xn;
+    int warm;
+    bool stats;
+    int plan, fixed, max_iter;
+    bool phi, trace;
+    bool operator==(const GraphKey &o) const {
+      return x == o.x && u == o.u && xn == o.xn && warm == o.warm && stats == o.stats && plan == o.plan &&
+             fixed == o.fixed && max_iter == o.max_iter && phi == o.phi && trace == o.trace;
+    }
+  };
+  struct GraphEntry {
+    GraphKey key;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t capture_stream = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
   ~dlmpc_ctx() {
@@ -123,6 +147,8 @@ struct dlmpc_ctx {
     if (h_err) cudaFreeHost(h_err);
     for (auto &e : ev)
       if (e) cudaEventDestroy(e);
+    for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
   }
   int fail(int code, const std::string &msg) {
     err = msg;
@@ -641,6 +667,7 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
     }
   }
   ctx->smem = (size_t)((int64_t)ng * ctx->grp_floats + cta_floats + used_max) * 4;
+  ++ctx->plan_version;
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem), "smem attr");
   int occ = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, gt * ng, ctx->smem), "occupancy");
@@ -768,23 +795,7 @@ extern "C" int dlmpc_precompute(dlmpc_ctx *ctx) {
 
 namespace {
 
-int run_step(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_dev, int warm, dlmpc_stats *stats) {
-  if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
-  if (warm != DLMPC_WARM_COLD && warm != DLMPC_WARM_PREVIOUS)
-    return ctx->fail(DLMPC_ERR_ARG, "unsupported warm-start mode");
-  cudaStream_t s = ctx->stream;
-  if (ctx->export_phi && ctx->d_phi.n != (size_t)ctx->state_floats) {
-    CK(ctx->d_phi.alloc(ctx->state_floats), "alloc Phi");
-    CK(cudaMemsetAsync(ctx->d_phi.p, 0, ctx->state_floats * 4, s), "memset");
-  }
-  ctx->timed_step = false;
-  if (ctx->timing) {
-    for (auto &e : ctx->ev)
-      if (!e) CK(cudaEventCreate(&e), "cudaEventCreate");
-    CK(cudaEventRecord(ctx->ev[0], s), "event");
-  }
-  CK(cudaMemsetAsync(ctx->d_bar.p, 0, 3 * sizeof(unsigned long long), s), "memset");
-  CK(cudaMemsetAsync(ctx->d_err.p, 0, 32, s), "memset");
+Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_dev, int warm) {
   Params P{};
   P.items = ctx->d_items.p;
   P.n_items = ctx->n_sub;
@@ -845,33 +856,99 @@ int run_step(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_dev, in
   P.grp_floats = ctx->grp_floats;
   P.cta_floats = ctx->cta_floats;
   P.max_local_inst = ctx->max_local_inst;
-  P.trace = nullptr;
+  P.trace = ctx->trace ? ctx->d_trace.p : nullptr;
+  return P;
+}
+
+// Enqueues one step: counter resets, the sweep, and (with stats) the
+// statistics kernel and the copies of statistics and error words to pinned
+// host memory.  `events` records the kernel-only events (not under capture).
+int enqueue_step(dlmpc_ctx *ctx, const Params &P, bool with_stats, bool events, cudaStream_t s) {
+  CK(cudaMemsetAsync(ctx->d_bar.p, 0, 3 * sizeof(unsigned long long), s), "memset");
+  CK(cudaMemsetAsync(ctx->d_err.p, 0, 32, s), "memset");
+  if (P.trace) CK(cudaMemsetAsync(ctx->d_trace.p, 0, ctx->d_trace.n * 8, s), "memset");
+  if (events) CK(cudaEventRecord(ctx->ev[1], s), "event");
+  CK(launch_sweep(P, ctx->gt, ctx->grid, ctx->smem, s), "sweep_kernel launch");
+  if (events) CK(cudaEventRecord(ctx->ev[2], s), "event");
+  if (with_stats) {
+    CK(launch_stats(ctx->d_inst_item_ptr.p, ctx->n_inst, ctx->d_item_r.p, ctx->d_item_s.p, ctx->d_inst_iters.p,
+                    ctx->d_err.p, ctx->fixed_iters, ctx->d_epsp.p, ctx->d_epsd.p, ctx->d_stats.p, s),
+       "stats_kernel");
+    CK(cudaMemcpyAsync(ctx->h_stats, ctx->d_stats.p, sizeof(dlmpc_stats) * ctx->n_inst, cudaMemcpyDeviceToHost, s),
+       "D2H stats");
+    CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err.p, 32, cudaMemcpyDeviceToHost, s), "D2H err");
+  }
+  return 0;
+}
+
+// Replays (capturing on first use) the CUDA graph of one step for this set of
+// pointers and options.
+int graph_step(dlmpc_ctx *ctx, const Params &P, bool with_stats) {
+  dlmpc_ctx::GraphKey key{P.x, P.u, P.x_next, P.warm, with_stats, ctx->plan_version, P.fixed_iters, P.max_iter,
+                          P.Phi != nullptr, P.trace != nullptr};
+  for (auto &ge : ctx->graphs)
+    if (ge.key == key) {
+      CK(cudaGraphLaunch(ge.exec, ctx->stream), "cudaGraphLaunch");
+      return 0;
+    }
+  // capture on a private stream (the caller's may be the legacy default
+  // stream, which cannot be captured); the graph is launched on the caller's
+  if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "stream");
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  int rc = enqueue_step(ctx, P, with_stats, false, ctx->capture_stream);
+  cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "end capture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaGraphInstantiate");
+  if (ctx->graphs.size() >= 8) {
+    cudaGraphExecDestroy(ctx->graphs.front().exec);
+    ctx->graphs.erase(ctx->graphs.begin());
+  }
+  ctx->graphs.push_back({key, exec});
+  CK(cudaGraphLaunch(exec, ctx->stream), "cudaGraphLaunch");
+  return 0;
+}
+
+}  // namespace
+extern "C" int dlmpc_get_timing(dlmpc_ctx *ctx, float *ms);
+namespace {
+
+int run_step(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_dev, int warm, dlmpc_stats *stats) {
+  if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
+  if (warm != DLMPC_WARM_COLD && warm != DLMPC_WARM_PREVIOUS)
+    return ctx->fail(DLMPC_ERR_ARG, "unsupported warm-start mode");
+  cudaStream_t s = ctx->stream;
+  if (ctx->export_phi && ctx->d_phi.n != (size_t)ctx->state_floats) {
+    CK(ctx->d_phi.alloc(ctx->state_floats), "alloc Phi");
+    CK(cudaMemsetAsync(ctx->d_phi.p, 0, ctx->state_floats * 4, s), "memset");
+  }
   if (ctx->trace) {
     const size_t n = (size_t)ctx->grid * kTraceIters * kTracePoints;
     if (ctx->d_trace.n != n) CK(ctx->d_trace.alloc(n), "alloc trace");
-    CK(cudaMemsetAsync(ctx->d_trace.p, 0, n * 8, s), "memset");
-    P.trace = ctx->d_trace.p;
   }
-  if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s), "event");
-  CK(launch_sweep(P, ctx->gt, ctx->grid, ctx->smem, s), "sweep_kernel launch");
-  if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], s), "event");
-  if (!stats) {
-    if (ctx->timing) {
-      CK(cudaEventRecord(ctx->ev[3], s), "event");
-      ctx->timed_step = true;
-    }
-    return DLMPC_OK;
+  ctx->timed_step = false;
+  if (ctx->timing) {
+    for (auto &e : ctx->ev)
+      if (!e) CK(cudaEventCreate(&e), "cudaEventCreate");
+    CK(cudaEventRecord(ctx->ev[0], s), "event");
   }
-  CK(launch_stats(ctx->d_inst_item_ptr.p, ctx->n_inst, ctx->d_item_r.p, ctx->d_item_s.p, ctx->d_inst_iters.p,
-                  ctx->d_err.p, ctx->fixed_iters, ctx->d_epsp.p, ctx->d_epsd.p, ctx->d_stats.p, s),
-     "stats_kernel");
-  CK(cudaMemcpyAsync(ctx->h_stats, ctx->d_stats.p, sizeof(dlmpc_stats) * ctx->n_inst, cudaMemcpyDeviceToHost, s),
-     "D2H stats");
-  CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err.p, 32, cudaMemcpyDeviceToHost, s), "D2H err");
+  const Params P = make_params(ctx, x_dev, u_dev, xn_dev, warm);
+  const bool with_stats = stats != nullptr;
+  ctx->kernel_events = !ctx->use_graph && ctx->timing;
+  int rc = ctx->use_graph ? graph_step(ctx, P, with_stats) : enqueue_step(ctx, P, with_stats, ctx->timing != 0, s);
+  if (rc) return rc;
   if (ctx->timing) {
     CK(cudaEventRecord(ctx->ev[3], s), "event");
     ctx->timed_step = true;
   }
+  if (!with_stats) return DLMPC_OK;
   CK(cudaStreamSynchronize(s), "step");
   if (ctx->h_err[0] != 0) {
     char buf[200];
@@ -936,6 +1013,119 @@ extern "C" int dlmpc_solve_batch(dlmpc_ctx *ctx, const float *const *x_dev, floa
   return rc;
 }
 
+namespace {
+
+// Best sweep launch per problem signature, shared by every context of the process.
+struct TuneSig {
+  int nx, nu, n_sub, n_inst, max_dcol, max_kpad, max_nmem;
+  int64_t work;
+  bool operator<(const TuneSig &o) const {
+    return std::tie(nx, nu, n_sub, n_inst, max_dcol, max_kpad, max_nmem, work) <
+           std::tie(o.nx, o.nu, o.n_sub, o.n_inst, o.max_dcol, o.max_kpad, o.max_nmem, o.work);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneSig, dlmpc_tune_entry> g_tune_cache;
+
+TuneSig signature(const dlmpc_ctx *ctx) {
+  int64_t work = 0;
+  for (const Item &it : ctx->items) work += (int64_t)it.dred * it.k;
+  return {ctx->nx, ctx->nu, ctx->n_sub, ctx->n_inst, ctx->max_dcol, ctx->max_kpad, ctx->max_nmem, work};
+}
+
+}  // namespace
+
+extern "C" int dlmpc_autotune(dlmpc_ctx *ctx, const float *x_dev, int32_t iters, dlmpc_tune_entry *entries,
+                              int32_t cap) {
+  if (!ctx || !x_dev) return DLMPC_ERR_ARG;
+  if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
+  const TuneSig sig = signature(ctx);
+  if (iters <= 0) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto f = g_tune_cache.find(sig);
+    if (f == g_tune_cache.end()) return ctx->fail(DLMPC_ERR_ARG, "no cached tuning for this problem shape");
+    ctx->residency = f->second.residency;
+    return plan_sweep(ctx, f->second.group_threads, f->second.groups_per_cta, f->second.wave, true);
+  }
+  cudaStream_t s = ctx->stream;
+  // keep the caller's state and options
+  DevBuf<float> psi_save, lam_save;
+  const size_t bytes = (size_t)ctx->state_floats * 4;
+  CK(psi_save.alloc(ctx->state_floats), "alloc");
+  CK(lam_save.alloc(ctx->state_floats), "alloc");
+  CK(cudaMemcpyAsync(psi_save.p, ctx->d_psi.p, bytes, cudaMemcpyDeviceToDevice, s), "save state");
+  CK(cudaMemcpyAsync(lam_save.p, ctx->d_lam.p, bytes, cudaMemcpyDeviceToDevice, s), "save state");
+  const int saved_fixed = ctx->fixed_iters, saved_res = ctx->residency, saved_graph = ctx->use_graph;
+  const int saved_gt = ctx->gt, saved_ng = ctx->ng, saved_wave = ctx->wave;
+  const int saved_timing = ctx->timing, saved_phi = ctx->export_phi, saved_trace = ctx->trace;
+  ctx->fixed_iters = iters;
+  ctx->use_graph = 0;
+  ctx->timing = 1;
+  ctx->export_phi = 0;
+  ctx->trace = 0;
+  std::vector<dlmpc_tune_entry> tried;
+  dlmpc_tune_entry best{0, 0, 0, 0, std::numeric_limits<float>::infinity()};
+  static const int kGt[] = {64, 128, 256};
+  static const int kNg[] = {1, 2, 4, 6, 8, 12, 16};
+  static const int kWave[] = {1, 2};
+  static const int kRes[] = {2, 1};
+  std::vector<std::tuple<int, int, int, int, int>> seen;
+  for (int res : kRes)
+    for (int gt : kGt)
+      for (int ng : kNg)
+        for (int wave : kWave) {
+          if (gt * ng > 1024 || gt * ng < 64) continue;
+          ctx->residency = res;
+          if (plan_sweep(ctx, gt, ng, wave, false) != 0) continue;
+          auto key = std::make_tuple(ctx->gt, ctx->ng, ctx->wave, res, ctx->grid);
+          if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+          seen.push_back(key);
+          float ms_best = std::numeric_limits<float>::infinity();
+          bool ok = true;
+          for (int rep = 0; rep < 2 && ok; ++rep) {
+            dlmpc_stats st[1];
+            std::vector<dlmpc_stats> stv(ctx->n_inst);
+            if (run_step(ctx, x_dev, ctx->d_u.p, nullptr, DLMPC_WARM_COLD, stv.data()) < 0) {
+              ok = false;
+              break;
+            }
+            (void)st;
+            float ms[2];
+            if (dlmpc_get_timing(ctx, ms) != 0) { ok = false; break; }
+            ms_best = std::min(ms_best, ms[0]);
+          }
+          if (!ok) continue;
+          dlmpc_tune_entry e{ctx->gt, ctx->ng, ctx->wave, res, ms_best};
+          tried.push_back(e);
+          if (ms_best < best.ms) best = e;
+        }
+  ctx->fixed_iters = saved_fixed;
+  ctx->use_graph = saved_graph;
+  ctx->timing = saved_timing;
+  ctx->export_phi = saved_phi;
+  ctx->trace = saved_trace;
+  CK(cudaMemcpyAsync(ctx->d_psi.p, psi_save.p, bytes, cudaMemcpyDeviceToDevice, s), "restore state");
+  CK(cudaMemcpyAsync(ctx->d_lam.p, lam_save.p, bytes, cudaMemcpyDeviceToDevice, s), "restore state");
+  CK(cudaStreamSynchronize(s), "autotune");
+  int rc;
+  if (best.group_threads == 0) {
+    ctx->residency = saved_res;
+    rc = plan_sweep(ctx, saved_gt, saved_ng, saved_wave, true);
+    if (rc == 0) rc = ctx->fail(DLMPC_ERR_ARG, "no sweep shape could be timed");
+    return rc;
+  }
+  ctx->residency = best.residency;
+  rc = plan_sweep(ctx, best.group_threads, best.groups_per_cta, best.wave, true);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[sig] = best;
+  }
+  if (entries)
+    for (int i = 0; i < (int)tried.size() && i < cap; ++i) entries[i] = tried[i];
+  return (int)tried.size();
+}
+
 extern "C" int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value) {
   if (!ctx) return DLMPC_ERR_ARG;
   switch (key) {
@@ -948,6 +1138,7 @@ extern "C" int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value) {
     case DLMPC_OPT_EXPORT_PHI: ctx->export_phi = value != 0; return 0;
     case DLMPC_OPT_TIMING: ctx->timing = value != 0; return 0;
     case DLMPC_OPT_TRACE: ctx->trace = value != 0; return 0;
+    case DLMPC_OPT_GRAPH: ctx->use_graph = value != 0; return 0;
     case DLMPC_OPT_RESIDENCY: {
       if (!(value >= 0 && value <= 2)) return ctx->fail(DLMPC_ERR_ARG, "residency must be 0, 1 or 2");
       ctx->residency = (int)value;
@@ -1073,8 +1264,9 @@ extern "C" int dlmpc_get_timing(dlmpc_ctx *ctx, float *ms) {
   if (!ctx || !ms) return DLMPC_ERR_ARG;
   if (!ctx->timed_step) return ctx->fail(DLMPC_ERR_ARG, "no timed step (enable DLMPC_OPT_TIMING)");
   CK(cudaEventSynchronize(ctx->ev[3]), "event sync");
-  CK(cudaEventElapsedTime(&ms[0], ctx->ev[1], ctx->ev[2]), "elapsed");
   CK(cudaEventElapsedTime(&ms[1], ctx->ev[0], ctx->ev[3]), "elapsed");
+  if (ctx->kernel_events) CK(cudaEventElapsedTime(&ms[0], ctx->ev[1], ctx->ev[2]), "elapsed");
+  else ms[0] = ms[1];
   return 0;
 }
 

@@ -213,3 +213,48 @@ def test_sweep_shapes_and_streaming(name, shape, torch):
     ref2 = O.admm(o.lay, o.blocks, p.x0, Psi0=ref.Psi, Lam0=ref.Lam, fixed_iters=K)
     assert rel(psi2, ref2.Psi) <= REL
     s.close()
+
+
+def test_graph_replay_is_bit_identical(torch):
+    """Steps replayed from captured CUDA graphs (one graph per buffer set of a
+    ping-pong closed loop) equal directly launched steps bit for bit."""
+    import paper_2103_14990_gb300 as pkg
+    p = SMALL["chain16_T10_d3_box"]()
+    outs = []
+    for graph in (0, 1):
+        s = gpu_solver([p], torch)
+        s.set_option(pkg.OPT_GRAPH, graph)
+        xa = torch.tensor(p.x0.astype(np.float32), device="cuda")
+        xb = torch.zeros_like(xa)
+        u = torch.zeros(p.n_sub, 1, device="cuda")
+        us, its = [], []
+        for tau in range(6):
+            rc, st = s.step(xa, u, xb, warm=pkg.WARM_COLD if tau == 0 else pkg.WARM_PREVIOUS)
+            us.append(u.cpu().numpy().copy())
+            its.append(st[0]["iters"])
+            xa, xb = xb, xa
+        outs.append((np.array(us), its))
+        s.close()
+    assert outs[0][1] == outs[1][1]
+    assert np.array_equal(outs[0][0], outs[1][0])
+
+
+def test_autotune_keeps_state_and_parity(torch):
+    import paper_2103_14990_gb300 as pkg
+    p = SMALL["grid5x5_T6_d2_box"]()
+    s = gpu_solver([p], torch)
+    x = torch.tensor(p.x0.astype(np.float32), device="cuda")
+    _, psi0, lam0 = s.get_state()
+    psi0, lam0 = psi0.clone(), lam0.clone()
+    table = s.autotune(x, iters=5)
+    assert len(table) >= 2 and all(e["ms"] > 0 for e in table)
+    _, psi1, lam1 = s.get_state()
+    assert torch.equal(psi0, psi1) and torch.equal(lam0, lam1)
+    best = table[0]
+    info = s.info()
+    assert (info["group_threads"], info["wave"]) == (best["group_threads"], best["wave"])
+    o = O.Oracle(p)
+    ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=30)
+    rc, st, phi, psi, lam, u, xn = run_fixed(s, torch, p.x0, 30)
+    assert rel(psi, ref.Psi) <= REL and rel(phi, ref.Phi) <= REL
+    s.close()
