@@ -55,6 +55,7 @@ extern "C" {
 #define DLMPC_WARM_LEARNED 2   /* learned initial Phi rows and Lambda, then a Psi-step first */
 
 typedef struct dlmpc_ctx dlmpc_ctx;
+typedef struct dlmpc_mlp dlmpc_mlp;
 
 /* One DLMPC instance: Eq. (MPC) of Sec. II-A with Q_t = Q, R_t = R for all t.
  * The coupling graph G_(A,B) is undirected, CSR, without self loops; column
@@ -114,6 +115,8 @@ typedef struct {
 #define DLMPC_OPT_GRAPH 10        /* != 0: run each step as a CUDA graph (captured on first use for
                                      a given set of buffers and options, then replayed); with it,
                                      dlmpc_get_timing reports the whole step in both fields */
+#define DLMPC_OPT_LEARN_PLANT 11  /* != 0: network inputs also carry each patch member's A_mm and
+                                     summed coupling blocks (set before dlmpc_attach_mlp) */
 #define DLMPC_OPT_RESIDENCY 8     /* shared-memory residency during a step: 0 none (all streamed),
                                      1 Psi/Lambda/q, 2 (default) also N where it fits; replans */
 
@@ -210,6 +213,48 @@ int dlmpc_get_timing(dlmpc_ctx *ctx, float *ms);
 int dlmpc_factor_patch_noalloc(const double *Z_dev, int32_t m, int32_t D, const double *rhs_dev,
                                int32_t nrhs, double *N_dev, int32_t k_cap, double *q_dev,
                                int32_t *rank_nullity_dev, double *feas_dev, void *stream);
+
+/* ---- learned warm start (Sec. V names a better ADMM starting point as future
+ * work; the network and its training are this library's, not the paper's) ----
+ *
+ * Network: x -> GELU(x W1 + b1) -> GELU(. W2 + b2) -> . W3 + b3, BF16 tensor-core
+ * GEMMs with FP32 accumulation, FP32 master parameters, AdamW.  Parameter
+ * block (FP32, in this order): W1 [d_in][hidden], b1 [hidden], W2
+ * [hidden][hidden], b2 [hidden], W3 [hidden][d_out], b3 [d_out]; row-major.
+ * The network predicts normalised outputs; forward returns y * scale + shift.
+ * Create the network on the same stream as the contexts it serves. */
+int dlmpc_mlp_create(int32_t d_in, int32_t hidden, int32_t d_out, void *stream, dlmpc_mlp **out);
+int64_t dlmpc_mlp_num_params(dlmpc_mlp *mlp);
+/* Sets the parameters (host, num_params floats) and the output scale/shift
+ * (host [d_out] each, NULL keeps them); resets the AdamW moments. */
+int dlmpc_mlp_set_params(dlmpc_mlp *mlp, const float *params, int64_t n, const float *out_scale,
+                         const float *out_shift);
+int dlmpc_mlp_get_params(dlmpc_mlp *mlp, float *params, int64_t n);
+/* y_dev [n][d_out] = de-normalised network output for x_dev [n][d_in] (device). */
+int dlmpc_mlp_forward(dlmpc_mlp *mlp, const float *x_dev, int32_t n, float *y_dev);
+/* Mean squared error against normalised targets t_dev [n][d_out] and its
+ * gradient w.r.t. every parameter (grad_host [num_params], may be NULL). */
+int dlmpc_mlp_gradients(dlmpc_mlp *mlp, const float *x_dev, const float *t_dev, int32_t n, float *grad_host,
+                        double *loss_host);
+/* One AdamW step (beta1 0.9, beta2 0.999, eps 1e-8, decoupled weight decay)
+ * on the batch; loss_host (may be NULL) receives the batch loss before it. */
+int dlmpc_mlp_train_step(dlmpc_mlp *mlp, const float *x_dev, const float *t_dev, int32_t n, float lr,
+                         float weight_decay, double *loss_host);
+const char *dlmpc_mlp_last_error(dlmpc_mlp *mlp);
+void dlmpc_mlp_destroy(dlmpc_mlp *mlp);
+
+/* Widths of the network input (patch state of a subsystem, members placed by
+ * position relative to it, zero padded) and output (its Phi rows then its
+ * Lambda rows over the same member slots: 2 * r_sub * slots * nx). */
+int dlmpc_learned_dims(dlmpc_ctx *ctx, int32_t *d_in, int32_t *d_out);
+/* feats_dev [n_sub_total][d_in] from x_dev (device). */
+int dlmpc_learned_features(dlmpc_ctx *ctx, const float *x_dev, float *feats_dev);
+/* targets_dev [n_sub_total][d_out]: the rows of the last Phi (needs
+ * DLMPC_OPT_EXPORT_PHI during the step) and of Lambda. */
+int dlmpc_learned_targets(dlmpc_ctx *ctx, float *targets_dev);
+/* Network used by DLMPC_WARM_LEARNED (NULL detaches): each step then starts
+ * from Psi0 = proj(Phi~ + Lambda~), Lambda0 = Lambda~ + Phi~ - Psi0. */
+int dlmpc_attach_mlp(dlmpc_ctx *ctx, dlmpc_mlp *mlp);
 
 /* One measured launch shape of the sweep kernel. */
 typedef struct {

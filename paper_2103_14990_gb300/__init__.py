@@ -38,6 +38,7 @@ OPT_TIMING = 7
 OPT_RESIDENCY = 8
 OPT_TRACE = 9
 OPT_GRAPH = 10
+OPT_LEARN_PLANT = 11
 
 # Every entry point declared in include/dlmpc.h (checked by the tests).
 EXPORTED = [
@@ -45,6 +46,10 @@ EXPORTED = [
     "dlmpc_set_option", "dlmpc_get_info", "dlmpc_get_state", "dlmpc_set_state",
     "dlmpc_get_patch", "dlmpc_get_operator", "dlmpc_get_timing", "dlmpc_get_trace", "dlmpc_last_error",
     "dlmpc_destroy", "dlmpc_autotune",
+    "dlmpc_mlp_create", "dlmpc_mlp_num_params", "dlmpc_mlp_set_params", "dlmpc_mlp_get_params",
+    "dlmpc_mlp_forward", "dlmpc_mlp_gradients", "dlmpc_mlp_train_step", "dlmpc_mlp_last_error",
+    "dlmpc_mlp_destroy", "dlmpc_learned_dims", "dlmpc_learned_features", "dlmpc_learned_targets",
+    "dlmpc_attach_mlp",
     "dlmpc_factor_patch_noalloc",
 ]
 
@@ -110,6 +115,23 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dlmpc_get_patch.argtypes = [vp, ctypes.c_int32, _ip, ctypes.c_int32]
     lib.dlmpc_get_operator.argtypes = [vp, ctypes.c_int32, _dp, ctypes.c_int32, _dp, ctypes.c_int32]
     lib.dlmpc_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.dlmpc_mlp_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, ctypes.POINTER(vp)]
+    lib.dlmpc_mlp_num_params.argtypes = [vp]
+    lib.dlmpc_mlp_num_params.restype = ctypes.c_int64
+    lib.dlmpc_mlp_set_params.argtypes = [vp, fp, ctypes.c_int64, fp, fp]
+    lib.dlmpc_mlp_get_params.argtypes = [vp, fp, ctypes.c_int64]
+    lib.dlmpc_mlp_forward.argtypes = [vp, vp, ctypes.c_int32, vp]
+    lib.dlmpc_mlp_gradients.argtypes = [vp, vp, vp, ctypes.c_int32, fp, ctypes.POINTER(ctypes.c_double)]
+    lib.dlmpc_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                         ctypes.POINTER(ctypes.c_double)]
+    lib.dlmpc_mlp_last_error.argtypes = [vp]
+    lib.dlmpc_mlp_last_error.restype = ctypes.c_char_p
+    lib.dlmpc_mlp_destroy.argtypes = [vp]
+    lib.dlmpc_mlp_destroy.restype = None
+    lib.dlmpc_learned_dims.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    lib.dlmpc_learned_features.argtypes = [vp, vp, vp]
+    lib.dlmpc_learned_targets.argtypes = [vp, vp]
+    lib.dlmpc_attach_mlp.argtypes = [vp, vp]
     lib.dlmpc_autotune.argtypes = [vp, vp, ctypes.c_int32, ctypes.POINTER(TuneEntry_C), ctypes.c_int32]
     lib.dlmpc_get_trace.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int64]
     lib.dlmpc_last_error.argtypes = [vp]
@@ -257,6 +279,30 @@ class Solver:
         out = [{f: getattr(arr[i], f) for f, _ in TuneEntry_C._fields_} for i in range(min(n, cap))]
         return sorted(out, key=lambda e: e["ms"])
 
+    def learned_dims(self):
+        a, o = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.dlmpc_learned_dims(self._ctx, ctypes.byref(a), ctypes.byref(o)))
+        return a.value, o.value
+
+    def learned_features(self, x):
+        d_in, _ = self.learned_dims()
+        out = self.torch.empty(self.n_sub, d_in, dtype=self.torch.float32, device="cuda")
+        self._check(self.lib.dlmpc_learned_features(self._ctx, ctypes.c_void_p(x.data_ptr()),
+                                                    ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def learned_targets(self):
+        """Phi rows then Lambda rows of every subsystem from the last step
+        (needs OPT_EXPORT_PHI during that step)."""
+        _, d_out = self.learned_dims()
+        out = self.torch.empty(self.n_sub, d_out, dtype=self.torch.float32, device="cuda")
+        self._check(self.lib.dlmpc_learned_targets(self._ctx, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def attach_mlp(self, mlp):
+        self._mlp = mlp
+        self._check(self.lib.dlmpc_attach_mlp(self._ctx, mlp._h if mlp is not None else None))
+
     def trace(self) -> np.ndarray:
         """[ctas, 8 iterations, 8 points] globaltimer stamps (ns) of the last step."""
         cap = 1 << 20
@@ -299,6 +345,92 @@ class Solver:
         if getattr(self, "_ctx", None) is not None and self._ctx.value:
             self.lib.dlmpc_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The warm-start network of the C ABI (x -> GELU -> GELU -> linear), BF16
+    tensor-core GEMMs, FP32 masters, AdamW.  Parameters are initialised here
+    (seeded, uniform +-1/sqrt(fan_in), zero biases) and uploaded."""
+
+    def __init__(self, d_in: int, hidden: int, d_out: int, stream=None, seed: int = 0):
+        import torch
+        self.lib = load_library()
+        self.torch = torch
+        self.d_in, self.hidden, self.d_out = d_in, hidden, d_out
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._h = ctypes.c_void_p()
+        rc = self.lib.dlmpc_mlp_create(d_in, hidden, d_out, ctypes.c_void_p(self.stream.cuda_stream),
+                                       ctypes.byref(self._h))
+        if rc != 0:
+            raise DlmpcError(rc, "dlmpc_mlp_create failed")
+        self.n_params = int(self.lib.dlmpc_mlp_num_params(self._h))
+        rng = np.random.default_rng(seed)
+        parts = []
+        for fan_in, fan_out in [(d_in, hidden), (hidden, hidden), (hidden, d_out)]:
+            lim = 1.0 / np.sqrt(fan_in)
+            parts.append(rng.uniform(-lim, lim, fan_in * fan_out))
+            parts.append(np.zeros(fan_out))
+        self.set_params(np.concatenate(parts).astype(np.float32))
+
+    def _check(self, rc):
+        if rc < 0:
+            raise DlmpcError(rc, self.lib.dlmpc_mlp_last_error(self._h).decode())
+        return rc
+
+    def unpack(self, p):
+        """dict W1, b1, W2, b2, W3, b3 (views) of a flat parameter vector."""
+        I, H, O = self.d_in, self.hidden, self.d_out
+        out, o = {}, 0
+        for name, shape in [("W1", (I, H)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (H, O)), ("b3", (O,))]:
+            n = int(np.prod(shape))
+            out[name] = p[o:o + n].reshape(shape)
+            o += n
+        return out
+
+    def set_params(self, params, scale=None, shift=None):
+        p = np.ascontiguousarray(params, np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        sc = np.ascontiguousarray(scale, np.float32) if scale is not None else None
+        sh = np.ascontiguousarray(shift, np.float32) if shift is not None else None
+        self._check(self.lib.dlmpc_mlp_set_params(self._h, _ptr(p, ctypes.c_float), p.size,
+                                                  _ptr(sc, ctypes.c_float), _ptr(sh, ctypes.c_float)))
+
+    def get_params(self):
+        p = np.zeros(self.n_params, np.float32)
+        self._check(self.lib.dlmpc_mlp_get_params(self._h, _ptr(p, ctypes.c_float), p.size))
+        return p
+
+    def forward(self, x):
+        y = self.torch.empty(x.shape[0], self.d_out, dtype=self.torch.float32, device="cuda")
+        self._check(self.lib.dlmpc_mlp_forward(self._h, ctypes.c_void_p(x.data_ptr()), x.shape[0],
+                                               ctypes.c_void_p(y.data_ptr())))
+        return y
+
+    def gradients(self, x, t):
+        g = np.zeros(self.n_params, np.float32)
+        loss = ctypes.c_double()
+        self._check(self.lib.dlmpc_mlp_gradients(self._h, ctypes.c_void_p(x.data_ptr()),
+                                                 ctypes.c_void_p(t.data_ptr()), x.shape[0],
+                                                 _ptr(g, ctypes.c_float), ctypes.byref(loss)))
+        return g, loss.value
+
+    def train_step(self, x, t, lr: float, weight_decay: float = 0.0, want_loss: bool = False):
+        loss = ctypes.c_double()
+        self._check(self.lib.dlmpc_mlp_train_step(self._h, ctypes.c_void_p(x.data_ptr()),
+                                                  ctypes.c_void_p(t.data_ptr()), x.shape[0], lr, weight_decay,
+                                                  ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.dlmpc_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
 
     def __del__(self):
         try:

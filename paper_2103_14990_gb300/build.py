@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdlmpc.so")
 
-SOURCES = ["dlmpc_kernels.cu", "dlmpc_sweep.cu", "dlmpc_host.cpp", "dlmpc_noalloc.cu"]
+SOURCES = ["dlmpc_kernels.cu", "dlmpc_sweep.cu", "dlmpc_learn.cu", "dlmpc_mlp.cu", "dlmpc_host.cpp",
+           "dlmpc_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -48,7 +49,7 @@ def _compile(src: str, verbose: bool) -> str:
 def build(verbose: bool = False) -> str:
     """Compiles every translation unit in parallel and links libdlmpc.so."""
     os.makedirs(BUILD, exist_ok=True)
-    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     tmp = LIB + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]

@@ -31,6 +31,21 @@ cudaError_t launch_stats(const int32_t *inst_item_ptr, int n_inst, const float *
                          const float *epsd, dlmpc_stats *out, cudaStream_t s);
 cudaError_t launch_gather(const float *const *src, const int32_t *off, int n_inst, int width, float *dst,
                           cudaStream_t s);
+struct LearnArgs {
+  const Item *items;
+  int n_items;
+  const int32_t *members;
+  const int32_t *rev_slot;
+  int nx, slots, L, max_rsub;
+  int d_out;
+  int plant;
+  const double *Adiag, *Aoff;
+  const int32_t *adj_ptr;
+};
+cudaError_t launch_learn_features(const LearnArgs &A, const float *x, float *feats, cudaStream_t s);
+cudaError_t launch_learn_rows(const LearnArgs &A, float *phi, float *lam, float *rows, int dir, cudaStream_t s);
+cudaError_t launch_learn_init(const Item *items, int n_items, int nx, int max_dred, int max_kpad, const float *Nmat,
+                              const float *qvec, const float *phi, float *psi, float *lam, cudaStream_t s);
 cudaError_t launch_scatter(const float *src, const int32_t *off, int n_inst, int width, float *const *dst,
                            cudaStream_t s);
 }  // namespace dlmpc
@@ -140,6 +155,10 @@ struct dlmpc_ctx {
   };
   std::vector<GraphEntry> graphs;
   cudaStream_t capture_stream = nullptr;
+  // learned warm start
+  dlmpc_mlp *mlp = nullptr;
+  int learn_L = 0, learn_slots = 1, learn_rsub = 1, learn_plant = 0;
+  DevBuf<float> d_feat, d_lout, d_phi_l;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
   ~dlmpc_ctx() {
@@ -795,6 +814,38 @@ extern "C" int dlmpc_precompute(dlmpc_ctx *ctx) {
 
 namespace {
 
+LearnArgs learn_args(dlmpc_ctx *ctx) {
+  int L = 0, slots = 1, rsub = 1;
+  for (const Item &it : ctx->items) L = std::max(L, it.self_pos);
+  for (const Item &it : ctx->items) {
+    slots = std::max(slots, L - it.self_pos + it.n_mem);
+    rsub = std::max(rsub, it.r_sub);
+  }
+  ctx->learn_L = L;
+  ctx->learn_slots = slots;
+  ctx->learn_rsub = rsub;
+  LearnArgs A{ctx->d_items.p, ctx->n_sub, ctx->d_members.p, ctx->d_rev.p, ctx->nx, slots, L, rsub,
+              2 * rsub * slots * ctx->nx, ctx->learn_plant, ctx->d_Adiag.p, ctx->d_Aoff.p, ctx->d_adj_ptr.p};
+  return A;
+}
+
+// Learned start (Sec. V "better initial point"): network Phi~ and Lambda~ rows
+// for every subsystem, then Psi0 = proj(Phi~ + Lambda~), Lambda0 = Lambda~ +
+// Phi~ - Psi0 written as the starting state.
+int learned_start(dlmpc_ctx *ctx, const float *x_dev) {
+  if (!ctx->mlp) return ctx->fail(DLMPC_ERR_ARG, "no network attached (dlmpc_attach_mlp)");
+  cudaStream_t s = ctx->stream;
+  const LearnArgs A = learn_args(ctx);
+  CK(launch_learn_features(A, x_dev, ctx->d_feat.p, s), "learn_features");
+  const int rc = dlmpc_mlp_forward(ctx->mlp, ctx->d_feat.p, ctx->n_sub, ctx->d_lout.p);
+  if (rc) return ctx->fail(rc, std::string("network forward: ") + dlmpc_mlp_last_error(ctx->mlp));
+  CK(launch_learn_rows(A, ctx->d_phi_l.p, ctx->d_lam.p, ctx->d_lout.p, 1, s), "learn_rows");
+  CK(launch_learn_init(ctx->d_items.p, ctx->n_sub, ctx->nx, ctx->max_dred_pad, ctx->max_kpad, ctx->d_N.p, ctx->d_q.p,
+                       ctx->d_phi_l.p, ctx->d_psi.p, ctx->d_lam.p, s),
+     "learn_init");
+  return 0;
+}
+
 Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_dev, int warm) {
   Params P{};
   P.items = ctx->d_items.p;
@@ -922,7 +973,7 @@ namespace {
 
 int run_step(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_dev, int warm, dlmpc_stats *stats) {
   if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
-  if (warm != DLMPC_WARM_COLD && warm != DLMPC_WARM_PREVIOUS)
+  if (warm != DLMPC_WARM_COLD && warm != DLMPC_WARM_PREVIOUS && warm != DLMPC_WARM_LEARNED)
     return ctx->fail(DLMPC_ERR_ARG, "unsupported warm-start mode");
   cudaStream_t s = ctx->stream;
   if (ctx->export_phi && ctx->d_phi.n != (size_t)ctx->state_floats) {
@@ -938,6 +989,11 @@ int run_step(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_dev, in
     for (auto &e : ctx->ev)
       if (!e) CK(cudaEventCreate(&e), "cudaEventCreate");
     CK(cudaEventRecord(ctx->ev[0], s), "event");
+  }
+  if (warm == DLMPC_WARM_LEARNED) {
+    const int lrc = learned_start(ctx, x_dev);
+    if (lrc) return lrc;
+    warm = DLMPC_WARM_PREVIOUS;  // the sweep continues from the learned start
   }
   const Params P = make_params(ctx, x_dev, u_dev, xn_dev, warm);
   const bool with_stats = stats != nullptr;
@@ -1035,6 +1091,8 @@ TuneSig signature(const dlmpc_ctx *ctx) {
 
 }  // namespace
 
+extern "C" int dlmpc_mlp_forward(dlmpc_mlp *mlp, const float *x_dev, int32_t n, float *y_dev);
+extern "C" const char *dlmpc_mlp_last_error(dlmpc_mlp *mlp);
 extern "C" int dlmpc_autotune(dlmpc_ctx *ctx, const float *x_dev, int32_t iters, dlmpc_tune_entry *entries,
                               int32_t cap) {
   if (!ctx || !x_dev) return DLMPC_ERR_ARG;
@@ -1139,6 +1197,7 @@ extern "C" int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value) {
     case DLMPC_OPT_TIMING: ctx->timing = value != 0; return 0;
     case DLMPC_OPT_TRACE: ctx->trace = value != 0; return 0;
     case DLMPC_OPT_GRAPH: ctx->use_graph = value != 0; return 0;
+    case DLMPC_OPT_LEARN_PLANT: ctx->learn_plant = value != 0; return 0;
     case DLMPC_OPT_RESIDENCY: {
       if (!(value >= 0 && value <= 2)) return ctx->fail(DLMPC_ERR_ARG, "residency must be 0, 1 or 2");
       ctx->residency = (int)value;
@@ -1188,6 +1247,43 @@ extern "C" int dlmpc_get_info(dlmpc_ctx *ctx, dlmpc_info *info) {
     bytes += dcol * 4;                               // row partial sums written
   }
   info->iter_bytes = bytes;
+  return 0;
+}
+
+extern "C" int dlmpc_learned_dims(dlmpc_ctx *ctx, int32_t *d_in, int32_t *d_out) {
+  if (!ctx || !ctx->precomputed) return ctx ? ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run") : DLMPC_ERR_ARG;
+  const LearnArgs A = learn_args(ctx);
+  if (d_in) *d_in = A.slots * (ctx->learn_plant ? ctx->nx + 2 * ctx->nx * ctx->nx : ctx->nx);
+  if (d_out) *d_out = A.d_out;
+  return 0;
+}
+
+extern "C" int dlmpc_learned_features(dlmpc_ctx *ctx, const float *x_dev, float *feats_dev) {
+  if (!ctx || !x_dev || !feats_dev) return DLMPC_ERR_ARG;
+  if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
+  const LearnArgs A = learn_args(ctx);
+  CK(launch_learn_features(A, x_dev, feats_dev, ctx->stream), "learn_features");
+  return 0;
+}
+
+extern "C" int dlmpc_learned_targets(dlmpc_ctx *ctx, float *targets_dev) {
+  if (!ctx || !targets_dev) return DLMPC_ERR_ARG;
+  if (!ctx->d_phi.p) return ctx->fail(DLMPC_ERR_ARG, "targets need the last Phi (DLMPC_OPT_EXPORT_PHI)");
+  const LearnArgs A = learn_args(ctx);
+  CK(launch_learn_rows(A, ctx->d_phi.p, ctx->d_lam.p, targets_dev, 0, ctx->stream), "learn_rows");
+  return 0;
+}
+
+extern "C" int dlmpc_attach_mlp(dlmpc_ctx *ctx, dlmpc_mlp *mlp) {
+  if (!ctx) return DLMPC_ERR_ARG;
+  if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
+  ctx->mlp = mlp;
+  if (!mlp) return 0;
+  const LearnArgs A = learn_args(ctx);
+  const int per = ctx->learn_plant ? ctx->nx + 2 * ctx->nx * ctx->nx : ctx->nx;
+  CK(ctx->d_feat.alloc((size_t)ctx->n_sub * A.slots * per), "alloc features");
+  CK(ctx->d_lout.alloc((size_t)ctx->n_sub * A.d_out), "alloc network output");
+  CK(ctx->d_phi_l.alloc(ctx->state_floats), "alloc learned Phi");
   return 0;
 }
 
