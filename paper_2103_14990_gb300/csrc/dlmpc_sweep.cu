@@ -31,14 +31,18 @@
 namespace dlmpc {
 
 struct GroupLayout {
-  int alpha, vred, psired, t, part, red, mtab, mbar, total;
+  int alpha, vred, psired, t, part, red, mtab, icache, mbar, total;
 };
+
+// Floats of one cached item: the Item, then rho, eps_p, eps_d, its own index.
+constexpr int kItemFloats = (int)((sizeof(Item) + 3) / 4) + 4;
 
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
 
-// Floats of one patch-member record: exchange offset, |Patch|, s, then
-// q[nx], x_lo[nx], x_hi[nx], r[nu], u_lo[nu], u_hi[nu].
-__host__ __device__ inline int member_record(int nx, int nu) { return 3 + 3 * nx + 3 * nu; }
+// Floats of one patch-member record: exchange read offset, |Patch|, 1/s (0
+// when s = 0), exchange write base, then x[nx], rho/(rho + 2 q s)[nx],
+// x_lo[nx], x_hi[nx], rho/(rho + 2 r s)[nu], u_lo[nu], u_hi[nu].
+__host__ __device__ inline int member_record(int nx, int nu) { return 4 + 4 * nx + 3 * nu; }
 
 // Float offsets inside one group region; the host uses the same function.
 __host__ __device__ inline GroupLayout group_layout(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad,
@@ -52,6 +56,7 @@ __host__ __device__ inline GroupLayout group_layout(int nx, int nu, int gt, int 
   L.part = o;   o += (gt / 32) * nx * max_kpad;
   L.red = o;    o += round4(4 * (gt / 32));
   L.mtab = o;   o += round4(wave * max_nmem * member_record(nx, nu));
+  L.icache = o; o += round4(wave * kItemFloats);
   L.mbar = o;   o += 4;
   L.total = o;
   return L;
@@ -68,38 +73,66 @@ __device__ __forceinline__ void group_sync(int g, int gt_threads) {
 }
 
 struct Group {
-  float *alpha, *vred, *psired, *t, *part, *mtab;
+  float *alpha, *vred, *psired, *t, *part, *mtab, *icache;
   double *red;
   uint64_t *mbar;
   unsigned phase;  // completed bulk copies on mbar
 };
 
-// Fills the member records of the wave's patches (one record per member).
+// Caches the wave's items (with their instance constants) and fills the
+// member records of their patches, so the iteration loop reads nothing but
+// the exchange sums (and non-resident N) from global memory.
 template <int NX>
-__device__ __forceinline__ void fill_members(const Params &P, const int *items, int wn, float *mtab, int gt, int GT) {
+__device__ __forceinline__ void fill_wave(const Params &P, const int *items, int wn, float *icache, float *mtab,
+                                          int gt, int GT) {
   const int MT = member_record(NX, P.nu);
+  constexpr int kItemWords = (int)((sizeof(Item) + 3) / 4);
+  for (int e = gt; e < wn * kItemWords; e += GT) {
+    const int wi = e / kItemWords, w = e % kItemWords;
+    reinterpret_cast<uint32_t *>(icache + wi * kItemFloats)[w] =
+        reinterpret_cast<const uint32_t *>(P.items + items[wi])[w];
+  }
+  for (int wi = gt; wi < wn; wi += GT) {
+    const Item &it = P.items[items[wi]];
+    float *ex = icache + wi * kItemFloats + kItemWords;
+    ex[0] = P.rho_i[it.inst];
+    ex[1] = P.epsp_i[it.inst];
+    ex[2] = P.epsd_i[it.inst];
+    reinterpret_cast<int *>(ex)[3] = items[wi];
+  }
   for (int wi = 0; wi < wn; ++wi) {
     const Item &it = P.items[items[wi]];
+    const float rho = P.rho_i[it.inst];
     float *tab = mtab + wi * P.max_nmem * MT;
     for (int e = gt; e < it.n_mem; e += GT) {
       const int m = P.members[it.mem_off + e];
       float *rec = tab + e * MT;
+      const float sm = __ldcg(P.S + m);
       reinterpret_cast<int *>(rec)[0] = (int)P.g_off[m];
       reinterpret_cast<int *>(rec)[1] = P.np_of[m];
-      rec[2] = __ldcg(P.S + m);
+      rec[2] = sm > 0.f ? 1.f / sm : 0.f;
+      reinterpret_cast<int *>(rec)[3] = (int)P.g_off[m] + P.rev_slot[it.mem_off + e] * it.r_sub;
 #pragma unroll
       for (int a = 0; a < NX; ++a) {
-        rec[3 + a] = P.qw[m * NX + a];
-        rec[3 + NX + a] = P.xlo[m * NX + a];
-        rec[3 + 2 * NX + a] = P.xhi[m * NX + a];
+        rec[4 + a] = P.x[(int64_t)m * NX + a];
+        rec[4 + NX + a] = rho / (rho + 2.f * P.qw[m * NX + a] * sm);
+        rec[4 + 2 * NX + a] = P.xlo[m * NX + a];
+        rec[4 + 3 * NX + a] = P.xhi[m * NX + a];
       }
       for (int bb = 0; bb < P.nu; ++bb) {
-        rec[3 + 3 * NX + bb] = P.rw[m * P.nu + bb];
-        rec[3 + 3 * NX + P.nu + bb] = P.ulo[m * P.nu + bb];
-        rec[3 + 3 * NX + 2 * P.nu + bb] = P.uhi[m * P.nu + bb];
+        rec[4 + 4 * NX + bb] = rho / (rho + 2.f * P.rw[m * P.nu + bb] * sm);
+        rec[4 + 4 * NX + P.nu + bb] = P.ulo[m * P.nu + bb];
+        rec[4 + 4 * NX + 2 * P.nu + bb] = P.uhi[m * P.nu + bb];
       }
     }
   }
+}
+
+__device__ __forceinline__ const Item &cached_item(const float *icache, int wi) {
+  return *reinterpret_cast<const Item *>(icache + wi * kItemFloats);
+}
+__device__ __forceinline__ const float *cached_extra(const float *icache, int wi) {
+  return icache + wi * kItemFloats + (int)((sizeof(Item) + 3) / 4);
 }
 
 // Phi-comp for every row of one patch (Sec. II-A row problem, closed form):
@@ -112,8 +145,9 @@ __device__ __forceinline__ void phi_rows(const Params &P, const Item &it, const 
   const int dcol = r_sub * it.n_mem;
   const int nxT = NX * it.T;
   const int MT = member_record(NX, P.nu);
+  const int dm = GT / r_sub, dr = GT - dm * r_sub;  // row stepping without division
+  int mpos = gt / r_sub, r = gt - mpos * r_sub;
   for (int f = gt; f < dcol; f += GT) {
-    const int mpos = f / r_sub, r = f - mpos * r_sub;
     const float *rec = tab + mpos * MT;
     const int goff = reinterpret_cast<const int *>(rec)[0];
     const int np = reinterpret_cast<const int *>(rec)[1];
@@ -127,39 +161,45 @@ __device__ __forceinline__ void phi_rows(const Params &P, const Item &it, const 
 #pragma unroll
       for (int j = 0; j < 8; ++j) w += gv[j];
     }
-    const float sm = rec[2];
-    float qwt, lo, hi;
+    const float inv_s = rec[2];
+    float den, lo, hi;
     if (r < nxT) {
       const int a = r % NX;
-      qwt = rec[3 + a];
+      den = rec[4 + NX + a];
       if (r >= NX) {
-        lo = rec[3 + NX + a];
-        hi = rec[3 + 2 * NX + a];
+        lo = rec[4 + 2 * NX + a];
+        hi = rec[4 + 3 * NX + a];
       } else {
         lo = -INFINITY;
         hi = INFINITY;
       }
     } else {
       const int bb = (r - nxT) % P.nu;
-      qwt = rec[3 + 3 * NX + bb];
-      lo = rec[3 + 3 * NX + P.nu + bb];
-      hi = rec[3 + 3 * NX + 2 * P.nu + bb];
+      den = rec[4 + 4 * NX + bb];
+      lo = rec[4 + 4 * NX + P.nu + bb];
+      hi = rec[4 + 4 * NX + 2 * P.nu + bb];
     }
+    // z* = rho w / (rho + 2 q s), clipped; alpha = (z - w) / s; s = 0 gives phi = v
     float a = 0.f, z = w;
-    if (sm > 0.f) {
-      const float z0 = rho * w / (rho + 2.f * qwt * sm);
-      z = fminf(fmaxf(z0, lo), hi);
-      a = (z - w) / sm;
+    if (inv_s > 0.f) {
+      z = fminf(fmaxf(w * den, lo), hi);
+      a = (z - w) * inv_s;
     }
     alpha_out[f] = a;
     if (mpos == it.self_pos && r >= nxT && r < nxT + P.nu) P.u[(int64_t)it.sub * P.nu + (r - nxT)] = z;
+    mpos += dm;
+    r += dr;
+    if (r >= r_sub) { r -= r_sub; ++mpos; }
   }
 }
 
 // Psi-comp, Lambda-comp and the residuals of one patch.
 template <int NX, int GT>
-__device__ void project_item(const Params &P, int idx, const Item &it, Group &G, const float *alpha, float *arena,
-                             float *Gnext, int g, int gt, float rho, unsigned *lnc, int iter) {
+__device__ void project_item(const Params &P, int idx, const Item &it, const float *tab, const float *extra, Group &G,
+                             const float *alpha, float *arena, float *Gnext, int g, int gt, unsigned *lnc, int iter,
+                             bool tr) {
+  const float rho = extra[0];
+  const int MT = member_record(NX, P.nu);
   const int r_sub = it.r_sub;
   const int dcol = r_sub * it.n_mem;
   const int rs_red = r_sub - NX;
@@ -172,11 +212,13 @@ __device__ void project_item(const Params &P, int idx, const Item &it, Group &G,
   const float *q_p = it.q_sm >= 0 ? arena + it.q_sm : P.qvec + it.q_off;
   float xj[NX];
 #pragma unroll
-  for (int c = 0; c < NX; ++c) xj[c] = P.x[(int64_t)it.sub * NX + c];
+  for (int c = 0; c < NX; ++c) xj[c] = tab[it.self_pos * MT + 4 + c];
 
   // v = Phi + Lambda = Psi + alpha x_hat(col), kept for the reduced rows
-  for (int f = gt; f < dcol; f += GT) {
-    const int mpos = f / r_sub, r = f - mpos * r_sub;
+  const int dm = GT / r_sub, dr = GT - dm * r_sub;  // row stepping without division
+  const int mpos0 = gt / r_sub, r0 = gt - mpos0 * r_sub;
+  for (int f = gt, mpos = mpos0, r = r0; f < dcol; f += GT, mpos += dm, r += dr) {
+    if (r >= r_sub) { r -= r_sub; ++mpos; }
     if (r >= NX) {
       const int red = mpos * rs_red + r - NX;
       const float a = alpha[f];
@@ -188,6 +230,7 @@ __device__ void project_item(const Params &P, int idx, const Item &it, Group &G,
   // generic 16-byte loads below serve both.
   const float *Nb = it.n_sm >= 0 ? arena + it.n_sm : P.Nmat + it.n_off;
   group_sync(g, GT);
+  if (tr) trace_point(P, iter, 6);
 
   // pass 1: t = N^T v.  Warp w takes row pairs (2i, 2i+1), i = w mod kWarps;
   // the half warp picks the row, the lane a group of 4 columns (blocks of 16
@@ -250,6 +293,7 @@ __device__ void project_item(const Params &P, int idx, const Item &it, Group &G,
     G.t[c * kpad + a] = (a < k) ? s : 0.f;  // padded columns of N are zero; keep t finite there
   }
   group_sync(g, GT);
+  if (tr) trace_point(P, iter, 7);
 
   // pass 2: psi_red = q + N t.  16 consecutive rows per half warp (conflict-
   // free with an odd number of 16-byte units per row); the two halves of a
@@ -298,11 +342,9 @@ __device__ void project_item(const Params &P, int idx, const Item &it, Group &G,
   group_sync(g, GT);
 
   // slot-0 states pinned to e_c; Lambda-comp; residuals; new exchange sums
-  const int *mem = P.members + it.mem_off;
-  const int *rev = P.rev_slot + it.mem_off;
-  float prim_f = 0.f, dual_f = 0.f;  // per-thread partials over a few rows, reduced in FP64
-  for (int f = gt; f < dcol; f += GT) {
-    const int mpos = f / r_sub, r = f - mpos * r_sub;
+  float prim_f = 0.f, dual_f = 0.f;  // FP32 partials per thread and warp, combined in FP64
+  for (int f = gt, mpos = mpos0, r = r0; f < dcol; f += GT, mpos += dm, r += dr) {
+    if (r >= r_sub) { r -= r_sub; ++mpos; }
     const int red = mpos * rs_red + r - NX;
     const float a = alpha[f];
     float gsum = 0.f;
@@ -322,13 +364,16 @@ __device__ void project_item(const Params &P, int idx, const Item &it, Group &G,
       if (P.Phi) P.Phi[it.st_off + c * dcol + f] = lam_new - lam_old + ps;
       gsum = fmaf(2.f * ps - vv, xj[c], gsum);
     }
-    Gnext[P.g_off[mem[mpos]] + (int64_t)rev[mpos] * r_sub + r] = gsum;
+    Gnext[reinterpret_cast<const int *>(tab + mpos * MT)[3] + r] = gsum;
   }
-  const double prim = warp_sum_d((double)prim_f);
-  const double dual = warp_sum_d((double)dual_f);
+  // GB300 runs FP64 at a small fraction of FP32: sums of a few squares stay in
+  // FP32 (tree order, relative error ~1e-6), the per-warp sums are combined
+  // in FP64 and Conv compares squared residuals (no square root on the path).
+  const float prim_w = warp_sum_f(prim_f);
+  const float dual_w = warp_sum_f(dual_f);
   if ((gt & 31) == 0) {
-    G.red[2 * (gt >> 5)] = prim;
-    G.red[2 * (gt >> 5) + 1] = dual;
+    G.red[2 * (gt >> 5)] = (double)prim_w;
+    G.red[2 * (gt >> 5) + 1] = (double)dual_w;
   }
   group_sync(g, GT);
   if (gt == 0) {
@@ -337,12 +382,15 @@ __device__ void project_item(const Params &P, int idx, const Item &it, Group &G,
       pp += G.red[2 * w];
       dd += G.red[2 * w + 1];
     }
-    const float rj = (float)sqrt(pp);
-    const float sj = (float)((double)rho * sqrt(dd));
+    const double epsp = extra[1], epsd = extra[2];
+    const double rho2 = (double)rho * (double)rho;
+    const bool conv = pp <= epsp * epsp && rho2 * dd <= epsd * epsd;
+    const float rj = sqrtf((float)pp);
+    const float sj = rho * sqrtf((float)dd);
     P.item_r[idx] = rj;
     P.item_s[idx] = sj;
     if (!(isfinite(rj) && isfinite(sj))) set_error(P.err, DLMPC_ERR_NONFINITE, blockIdx.x, iter, it.sub);
-    if (!(rj <= P.epsp_i[it.inst] && sj <= P.epsd_i[it.inst])) atomicAdd(lnc + it.lslot, 1u);
+    if (!conv) atomicAdd(lnc + it.lslot, 1u);
   }
 }
 
@@ -404,6 +452,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
   G.part = gbase + L.part;
   G.red = reinterpret_cast<double *>(gbase + L.red);
   G.mtab = gbase + L.mtab;
+  G.icache = gbase + L.icache;
   G.mbar = reinterpret_cast<uint64_t *>(gbase + L.mbar);
   G.phase = 0;
   float *cta = sm + P.ng * P.grp_floats;
@@ -477,7 +526,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
   ok = sweep_barrier(P, e_bar++, 0u, prev_hi, total, -1);
   // s_m of every member is now visible: single-wave groups fill their tables once
   if (ok && one_wave && gi1 > gi0) {
-    fill_members<NX>(P, P.grp_items + gi0, gi1 - gi0, G.mtab, gt, GT);
+    fill_wave<NX>(P, P.grp_items + gi0, gi1 - gi0, G.icache, G.mtab, gt, GT);
     group_sync(g, GT);
   }
 
@@ -504,23 +553,24 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
     for (int w0 = gi0; w0 < gi1; w0 += P.wave) {
       const int wn = min(P.wave, gi1 - w0);
       if (!one_wave) {
-        fill_members<NX>(P, P.grp_items + w0, wn, G.mtab, gt, GT);
+        group_sync(g, GT);  // the previous wave is done with the cache
+        fill_wave<NX>(P, P.grp_items + w0, wn, G.icache, G.mtab, gt, GT);
         group_sync(g, GT);
       }
       for (int wi = 0; wi < wn; ++wi) {
-        const Item &it = P.items[P.grp_items[w0 + wi]];
+        const Item &it = cached_item(G.icache, wi);
         if (!lact[it.lslot]) continue;
         phi_rows<NX, GT>(P, it, G.mtab + wi * P.max_nmem * MT, Gcur, G.alpha + wi * P.max_dcol,
-                         P.rho_i[it.inst], gt);
+                         cached_extra(G.icache, wi)[0], gt);
       }
       group_sync(g, GT);
       if (w0 == gi0) trace_point(P, iter, 1);
       for (int wi = 0; wi < wn; ++wi) {
-        const int idx = P.grp_items[w0 + wi];
-        const Item it = P.items[idx];
+        const Item &it = cached_item(G.icache, wi);
         if (!lact[it.lslot]) continue;
-        project_item<NX, GT>(P, idx, it, G, G.alpha + wi * P.max_dcol, arena, Gnext, g, gt, P.rho_i[it.inst], lnc,
-                             iter);
+        const float *ex = cached_extra(G.icache, wi);
+        project_item<NX, GT>(P, reinterpret_cast<const int *>(ex)[3], it, G.mtab + wi * P.max_nmem * MT, ex, G,
+                             G.alpha + wi * P.max_dcol, arena, Gnext, g, gt, lnc, iter, w0 == gi0 && wi == 0);
         if (w0 == gi0 && wi == 0) trace_point(P, iter, 2);
       }
       group_sync(g, GT);
