@@ -576,7 +576,8 @@ std::vector<std::vector<int32_t>> lpt(const dlmpc_ctx *ctx, const std::vector<in
 // groups by longest processing time, then each CTA's shared-memory arena
 // filled with resident Psi/Lambda and q, then resident N, until it is full.
 int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = false) {
-  if (!(gt == 64 || gt == 128 || gt == 256) || ng < 1 || gt * ng > 1024 || wave < 1 || wave > 8)
+  // named barrier ids 1..15 serve the groups (id 0 is __syncthreads)
+  if (!(gt == 64 || gt == 128 || gt == 256) || ng < 1 || ng > 15 || gt * ng > 1024 || wave < 1 || wave > 8)
     return ctx->fail(DLMPC_ERR_ARG, "unsupported sweep shape");
   if (ctx->max_kpad > 4 * gt) return ctx->fail(DLMPC_ERR_ARG, "null-space dimension too large for this group size");
   const int nx = ctx->nx;
@@ -1124,7 +1125,7 @@ extern "C" int dlmpc_autotune(dlmpc_ctx *ctx, const float *x_dev, int32_t iters,
   std::vector<dlmpc_tune_entry> tried;
   dlmpc_tune_entry best{0, 0, 0, 0, std::numeric_limits<float>::infinity()};
   static const int kGt[] = {64, 128, 256};
-  static const int kNg[] = {1, 2, 4, 6, 8, 12, 16};
+  static const int kNg[] = {1, 2, 4, 6, 8, 12, 15};
   static const int kWave[] = {1, 2};
   static const int kRes[] = {2, 1};
   std::vector<std::tuple<int, int, int, int, int>> seen;

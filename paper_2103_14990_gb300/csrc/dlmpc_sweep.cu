@@ -68,6 +68,7 @@ __device__ __forceinline__ void trace_point(const Params &P, int iter, int point
     P.trace[((size_t)blockIdx.x * kTraceIters + iter) * kTracePoints + point] = global_ns();
 }
 
+// Named barrier 1 + g (ids 1..15; the host limits a CTA to 15 groups).
 __device__ __forceinline__ void group_sync(int g, int gt_threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(gt_threads) : "memory");
 }

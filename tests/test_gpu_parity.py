@@ -182,7 +182,8 @@ def test_max_iter_status(torch):
     s.close()
 
 
-SHAPES = [(128, 4, 2, 2), (128, 4, 1, 0), (64, 8, 3, 1), (256, 2, 2, 0), (128, 1, 1, 2), (64, 2, 4, 0)]
+SHAPES = [(128, 4, 2, 2), (128, 4, 1, 0), (64, 8, 3, 1), (256, 2, 2, 0), (128, 1, 1, 2), (64, 2, 4, 0),
+          (64, 15, 2, 1)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -237,6 +238,15 @@ def test_graph_replay_is_bit_identical(torch):
         s.close()
     assert outs[0][1] == outs[1][1]
     assert np.array_equal(outs[0][0], outs[1][0])
+
+
+def test_sweep_shape_rejects_sixteen_groups(torch):
+    """Groups synchronise on named barriers 1..15: a 16th group is refused."""
+    import paper_2103_14990_gb300 as pkg
+    s = gpu_solver([SMALL["grid5x5_T6_d2_box"]()], torch)
+    with pytest.raises(pkg.DlmpcError):
+        s.set_option(pkg.OPT_SWEEP_SHAPE, 64 * 10000 + 16 * 100 + 1)
+    s.close()
 
 
 def test_autotune_keeps_state_and_parity(torch):
