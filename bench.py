@@ -198,6 +198,18 @@ def run_ours(args):
     plain = {"value": args.steps / (sum(ps) / 1e3), "unit": UNIT,
              "admm_iters_per_s": sum(pit) / (sum(pk) / 1e3), "iters_per_step": sum(pit) / len(pit)}
 
+    # ablation of the paper's GPU mappings (Sec. III): ADMM iterations/s from x(0)
+    ablation = {}
+    if not args.no_ablation:
+        names = {0: "naive (Sec. III-A)", 1: "combined (Sec. III-C)", 2: "persistent column patch (this library)"}
+        for v, it_n in ((0, args.ablation_iters), (1, args.ablation_iters), (2, 10 * args.ablation_iters)):
+            solver.run_variant(v, x0, 2)  # warm-up
+            ms = solver.run_variant(v, x0, it_n)
+            ablation[names[v]] = {"admm_iters_per_s": round(1e3 * it_n / ms, 1), "iters": it_n}
+        base = ablation[names[0]]["admm_iters_per_s"]
+        for v in ablation.values():
+            v["speedup_vs_naive"] = round(v["admm_iters_per_s"] / base, 2)
+
     # e2e: host (pinned) buffers through the C ABI, H2D and D2H inside the timed region
     xh = torch.empty(n, nx, dtype=torch.float32, pin_memory=True)
     xnh = torch.empty(n, nx, dtype=torch.float32, pin_memory=True)
@@ -239,6 +251,7 @@ def run_ours(args):
         "e2e": e2e,
         "roofline": roofline,
         "graph": graph,
+        "ablation": ablation,
         "sweep": {"group_threads": info["group_threads"], "groups_per_cta": info["groups_per_cta"],
                   "wave": info["wave"], "grid_ctas": info["grid_ctas"], "smem_bytes": info["smem_bytes"],
                   "resident_n_items": info["resident_n_items"],
@@ -377,6 +390,8 @@ def main():
     ap.add_argument("--workload", default="chain1024")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--ablation-iters", type=int, default=20)
     ap.add_argument("--tune-iters", type=int, default=20)
     ap.add_argument("--sample-seconds", type=float, default=15.0)
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)

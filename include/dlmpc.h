@@ -256,6 +256,18 @@ int dlmpc_learned_targets(dlmpc_ctx *ctx, float *targets_dev);
  * from Psi0 = proj(Phi~ + Lambda~), Lambda0 = Lambda~ + Phi~ - Psi0. */
 int dlmpc_attach_mlp(dlmpc_ctx *ctx, dlmpc_mlp *mlp);
 
+/* Ablation of the paper's GPU mappings (Sec. III): variant 0 = naive (one
+ * kernel per ADMM step, thread per row/column/element, every step's result
+ * shared through host memory, Conv flag read each iteration, Sec. III-A);
+ * 1 = combined (Phi kernel, then one Psi+Lambda+Conv kernel per column, one
+ * host exchange per iteration, Sec. III-C); 2 = the persistent column-patch
+ * sweep of this library.  Runs exactly `iters` iterations from `warm`
+ * (COLD or PREVIOUS) on x_dev, leaves Phi (allocating it if needed), Psi and
+ * Lambda in the context, and writes the host wall time to *ms_out.
+ * Requires null-space dimensions <= 256.  Synchronous. */
+int dlmpc_run_variant(dlmpc_ctx *ctx, int32_t variant, const float *x_dev, int32_t iters, int32_t warm,
+                      double *ms_out);
+
 /* One measured launch shape of the sweep kernel. */
 typedef struct {
   int32_t group_threads, groups_per_cta, wave, residency;

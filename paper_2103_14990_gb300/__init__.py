@@ -49,7 +49,7 @@ EXPORTED = [
     "dlmpc_mlp_create", "dlmpc_mlp_num_params", "dlmpc_mlp_set_params", "dlmpc_mlp_get_params",
     "dlmpc_mlp_forward", "dlmpc_mlp_gradients", "dlmpc_mlp_train_step", "dlmpc_mlp_last_error",
     "dlmpc_mlp_destroy", "dlmpc_learned_dims", "dlmpc_learned_features", "dlmpc_learned_targets",
-    "dlmpc_attach_mlp",
+    "dlmpc_attach_mlp", "dlmpc_run_variant",
     "dlmpc_factor_patch_noalloc",
 ]
 
@@ -132,6 +132,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dlmpc_learned_features.argtypes = [vp, vp, vp]
     lib.dlmpc_learned_targets.argtypes = [vp, vp]
     lib.dlmpc_attach_mlp.argtypes = [vp, vp]
+    lib.dlmpc_run_variant.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_double)]
     lib.dlmpc_autotune.argtypes = [vp, vp, ctypes.c_int32, ctypes.POINTER(TuneEntry_C), ctypes.c_int32]
     lib.dlmpc_get_trace.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int64]
     lib.dlmpc_last_error.argtypes = [vp]
@@ -302,6 +304,13 @@ class Solver:
     def attach_mlp(self, mlp):
         self._mlp = mlp
         self._check(self.lib.dlmpc_attach_mlp(self._ctx, mlp._h if mlp is not None else None))
+
+    def run_variant(self, variant: int, x, iters: int, warm: int = WARM_COLD) -> float:
+        """Paper mapping ablation (0 naive, 1 combined, 2 persistent sweep); host ms."""
+        ms = ctypes.c_double()
+        self._check(self.lib.dlmpc_run_variant(self._ctx, variant, ctypes.c_void_p(x.data_ptr()), iters, warm,
+                                               ctypes.byref(ms)))
+        return ms.value
 
     def trace(self) -> np.ndarray:
         """[ctas, 8 iterations, 8 points] globaltimer stamps (ns) of the last step."""

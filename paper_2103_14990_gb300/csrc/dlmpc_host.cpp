@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -43,6 +44,27 @@ struct LearnArgs {
   const int32_t *adj_ptr;
 };
 cudaError_t launch_learn_features(const LearnArgs &A, const float *x, float *feats, cudaStream_t s);
+struct VariantArgs {
+  const Item *items;
+  int n_items;
+  const int32_t *members;
+  const int32_t *rev_slot;
+  const float *Nmat, *qvec;
+  float *Phi, *Psi, *Lam, *PsiPrev;
+  const float *x;
+  float *S;
+  const float *qw, *rw, *xlo, *xhi, *ulo, *uhi;
+  const float *rho_i, *epsp_i, *epsd_i;
+  int nx, nu;
+  unsigned *notconv;
+};
+cudaError_t launch_variant_s(const VariantArgs &A, cudaStream_t s);
+cudaError_t launch_variant_phi(const VariantArgs &A, const int32_t *row_sub, const int32_t *row_loc, int total,
+                               cudaStream_t s);
+cudaError_t launch_variant_psi(const VariantArgs &A, cudaStream_t s);
+cudaError_t launch_variant_lambda(const VariantArgs &A, int64_t n, cudaStream_t s);
+cudaError_t launch_variant_conv(const VariantArgs &A, cudaStream_t s);
+cudaError_t launch_variant_combined(const VariantArgs &A, cudaStream_t s);
 cudaError_t launch_learn_rows(const LearnArgs &A, float *phi, float *lam, float *rows, int dir, cudaStream_t s);
 cudaError_t launch_learn_init(const Item *items, int n_items, int nx, int max_dred, int max_kpad, const float *Nmat,
                               const float *qvec, const float *phi, float *psi, float *lam, cudaStream_t s);
@@ -159,6 +181,10 @@ struct dlmpc_ctx {
   dlmpc_mlp *mlp = nullptr;
   int learn_L = 0, learn_slots = 1, learn_rsub = 1, learn_plant = 0;
   DevBuf<float> d_feat, d_lout, d_phi_l;
+  // paper-variant ablation
+  DevBuf<float> d_psi_prev;
+  DevBuf<int32_t> d_row_sub, d_row_loc;
+  float *h_exchange = nullptr;  // pinned, state_floats
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
   ~dlmpc_ctx() {
@@ -168,6 +194,7 @@ struct dlmpc_ctx {
       if (e) cudaEventDestroy(e);
     for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
     if (capture_stream) cudaStreamDestroy(capture_stream);
+    if (h_exchange) cudaFreeHost(h_exchange);
   }
   int fail(int code, const std::string &msg) {
     err = msg;
@@ -1285,6 +1312,84 @@ extern "C" int dlmpc_attach_mlp(dlmpc_ctx *ctx, dlmpc_mlp *mlp) {
   CK(ctx->d_feat.alloc((size_t)ctx->n_sub * A.slots * per), "alloc features");
   CK(ctx->d_lout.alloc((size_t)ctx->n_sub * A.d_out), "alloc network output");
   CK(ctx->d_phi_l.alloc(ctx->state_floats), "alloc learned Phi");
+  return 0;
+}
+
+// The paper's GPU mappings (Sec. III-A naive, Sec. III-C combined) for the
+// ablation; variant 2 is the persistent sweep.  Runs `iters` ADMM iterations
+// from a cold or previous start on x_dev and reports the host wall time.
+extern "C" int dlmpc_run_variant(dlmpc_ctx *ctx, int32_t variant, const float *x_dev, int32_t iters, int32_t warm,
+                                 double *ms_out) {
+  if (!ctx || !x_dev || iters < 1 || variant < 0 || variant > 2 || !ms_out) return DLMPC_ERR_ARG;
+  if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
+  cudaStream_t s = ctx->stream;
+  for (const Item &it : ctx->items)
+    if (it.k > 256) return ctx->fail(DLMPC_ERR_ARG, "variants need null spaces of dimension <= 256");
+  if (!ctx->d_phi.p || ctx->d_phi.n != (size_t)ctx->state_floats) {
+    CK(ctx->d_phi.alloc(ctx->state_floats), "alloc Phi");
+    CK(cudaMemsetAsync(ctx->d_phi.p, 0, ctx->state_floats * 4, s), "memset");
+  }
+  if (!ctx->d_psi_prev.p) CK(ctx->d_psi_prev.alloc(ctx->state_floats), "alloc");
+  if (!ctx->h_exchange) CK(cudaMallocHost(&ctx->h_exchange, ctx->state_floats * 4), "alloc pinned");
+  if (!ctx->d_row_sub.p) {
+    std::vector<int32_t> rs, rl;
+    for (int i = 0; i < ctx->n_sub; ++i)
+      for (int r = 0; r < ctx->items[i].r_sub; ++r) {
+        rs.push_back(i);
+        rl.push_back(r);
+      }
+    CK(upload(ctx->d_row_sub, rs, s), "upload rows");
+    CK(upload(ctx->d_row_loc, rl, s), "upload rows");
+  }
+  const int total_rows = (int)ctx->d_row_sub.n;
+  const int64_t nst = ctx->state_floats;
+  if (warm == DLMPC_WARM_COLD) {
+    CK(cudaMemsetAsync(ctx->d_psi.p, 0, nst * 4, s), "memset");
+    CK(cudaMemsetAsync(ctx->d_lam.p, 0, nst * 4, s), "memset");
+  }
+  CK(cudaStreamSynchronize(s), "variant setup");
+  auto t0 = std::chrono::steady_clock::now();
+  if (variant == 2) {
+    const int saved_fixed = ctx->fixed_iters, saved_phi = ctx->export_phi;
+    ctx->fixed_iters = iters;
+    ctx->export_phi = 1;
+    std::vector<dlmpc_stats> st(ctx->n_inst);
+    int rc = run_step(ctx, x_dev, ctx->d_u.p, nullptr, warm == DLMPC_WARM_COLD ? DLMPC_WARM_PREVIOUS : warm, st.data());
+    ctx->fixed_iters = saved_fixed;
+    ctx->export_phi = saved_phi;
+    if (rc < 0) return rc;
+  } else {
+    VariantArgs A{ctx->d_items.p, ctx->n_sub, ctx->d_members.p, ctx->d_rev.p, ctx->d_N.p, ctx->d_q.p,
+                  ctx->d_phi.p, ctx->d_psi.p, ctx->d_lam.p, ctx->d_psi_prev.p, x_dev, ctx->d_S.p,
+                  ctx->d_qw.p, ctx->d_rw.p, ctx->d_xlo.p, ctx->d_xhi.p, ctx->d_ulo.p, ctx->d_uhi.p,
+                  ctx->d_rho.p, ctx->d_epsp.p, ctx->d_epsd.p, ctx->nx, ctx->nu, ctx->d_notconv.p};
+    // information sharing through host memory, as in the paper's implementation
+    auto exchange = [&](float *dev) -> int {
+      CK(cudaMemcpyAsync(ctx->h_exchange, dev, nst * 4, cudaMemcpyDeviceToHost, s), "exchange D2H");
+      CK(cudaMemcpyAsync(dev, ctx->h_exchange, nst * 4, cudaMemcpyHostToDevice, s), "exchange H2D");
+      return 0;
+    };
+    CK(launch_variant_s(A, s), "variant s");
+    unsigned flag = 0;
+    for (int it = 0; it < iters; ++it) {
+      CK(cudaMemsetAsync(ctx->d_notconv.p, 0, 4, s), "memset");
+      CK(launch_variant_phi(A, ctx->d_row_sub.p, ctx->d_row_loc.p, total_rows, s), "variant phi");
+      if (exchange(ctx->d_phi.p)) return DLMPC_ERR_CUDA;
+      if (variant == 0) {
+        CK(launch_variant_psi(A, s), "variant psi");
+        if (exchange(ctx->d_psi.p)) return DLMPC_ERR_CUDA;
+        CK(launch_variant_lambda(A, nst, s), "variant lambda");
+        if (exchange(ctx->d_lam.p)) return DLMPC_ERR_CUDA;
+        CK(launch_variant_conv(A, s), "variant conv");
+      } else {
+        CK(launch_variant_combined(A, s), "variant combined");
+      }
+      CK(cudaMemcpyAsync(&flag, ctx->d_notconv.p, 4, cudaMemcpyDeviceToHost, s), "flag");
+      CK(cudaStreamSynchronize(s), "variant iteration");
+    }
+  }
+  CK(cudaStreamSynchronize(s), "variant");
+  *ms_out = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return 0;
 }
 

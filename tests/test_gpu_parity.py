@@ -268,3 +268,21 @@ def test_autotune_keeps_state_and_parity(torch):
     rc, st, phi, psi, lam, u, xn = run_fixed(s, torch, p.x0, 30)
     assert rel(psi, ref.Psi) <= REL and rel(phi, ref.Phi) <= REL
     s.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("name", ["chain16_T10_d3_box", "grid5x5_T6_d2_box"])
+def test_paper_variants_match_oracle(name, variant, torch):
+    """The paper's naive and combined GPU mappings and the persistent sweep
+    compute the same iterates as the oracle."""
+    p = SMALL[name]()
+    o = O.Oracle(p)
+    K = 12
+    ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=K)
+    s = gpu_solver([p], torch)
+    x = torch.tensor(p.x0.astype(np.float32), device="cuda")
+    ms = s.run_variant(variant, x, K)
+    assert ms > 0
+    phi, psi, lam = [a.cpu().numpy() for a in s.get_state(phi=True)]
+    assert rel(psi, ref.Psi) <= REL and rel(lam, ref.Lam) <= REL and rel(phi, ref.Phi) <= REL
+    s.close()
