@@ -118,6 +118,19 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 
+def replica_throughput(t_local: float, steps: int, world: int, dist=None, device: str = "cpu"):
+    """Whole-job MPC steps/s of `world` independent replicas that each ran
+    `steps` steps: all ranks' units over the slowest rank's time (max over
+    ranks).  Returns (value, max time)."""
+    t = t_local
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return world * steps / t, t
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -177,12 +190,7 @@ def run_ours(args):
         kms, sms, iters, status, xK = loop(args.steps, pkg.WARM_PREVIOUS)
         sync_all()
         wall = time.perf_counter() - wall0
-    t_dev = sum(sms) / 1e3
-    if dist is not None:
-        tt = torch.tensor([t_dev], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
-    value = world * args.steps / t_dev
+    value, t_dev = replica_throughput(sum(sms) / 1e3, args.steps, world, dist, device="cuda")
     kern_s = sum(kms) / 1e3
     tot_iters = sum(iters)
 

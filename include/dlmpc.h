@@ -117,6 +117,10 @@ typedef struct {
                                      dlmpc_get_timing reports the whole step in both fields */
 #define DLMPC_OPT_LEARN_PLANT 11  /* != 0: network inputs also carry each patch member's A_mm and
                                      summed coupling blocks (set before dlmpc_attach_mlp) */
+#define DLMPC_OPT_TEST_SKIP_ARRIVAL 12 /* test of failure handling: CTA `value` of the sweep leaves
+                                          before its first iteration barrier, so every other CTA's
+                                          bounded wait runs out and the step returns
+                                          DLMPC_ERR_TIMEOUT (-1 = off, the default) */
 #define DLMPC_OPT_RESIDENCY 8     /* shared-memory residency during a step: 0 none (all streamed),
                                      1 Psi/Lambda/q, 2 (default) also N where it fits; replans */
 

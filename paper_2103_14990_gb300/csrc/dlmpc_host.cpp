@@ -180,6 +180,7 @@ struct dlmpc_ctx {
   // learned warm start
   dlmpc_mlp *mlp = nullptr;
   int learn_L = 0, learn_slots = 1, learn_rsub = 1, learn_plant = 0;
+  int skip_arrival_cta = -1;
   DevBuf<float> d_feat, d_lout, d_phi_l;
   // paper-variant ablation
   DevBuf<float> d_psi_prev;
@@ -936,6 +937,7 @@ Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_d
   P.cta_floats = ctx->cta_floats;
   P.max_local_inst = ctx->max_local_inst;
   P.trace = ctx->trace ? ctx->d_trace.p : nullptr;
+  P.skip_arrival_cta = ctx->skip_arrival_cta;
   return P;
 }
 
@@ -1226,6 +1228,7 @@ extern "C" int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value) {
     case DLMPC_OPT_TRACE: ctx->trace = value != 0; return 0;
     case DLMPC_OPT_GRAPH: ctx->use_graph = value != 0; return 0;
     case DLMPC_OPT_LEARN_PLANT: ctx->learn_plant = value != 0; return 0;
+    case DLMPC_OPT_TEST_SKIP_ARRIVAL: ctx->skip_arrival_cta = (int)value; return 0;
     case DLMPC_OPT_RESIDENCY: {
       if (!(value >= 0 && value <= 2)) return ctx->fail(DLMPC_ERR_ARG, "residency must be 0, 1 or 2");
       ctx->residency = (int)value;

@@ -87,6 +87,8 @@ struct Params {
   int32_t cta_floats;         // floats of the per-CTA counters (after the group regions)
   int32_t max_local_inst;
   unsigned long long *trace;  // optional [grid][kTraceIters][kTracePoints] globaltimer stamps
+  int32_t skip_arrival_cta;   // test of the bounded waits: this CTA leaves before its first
+                              // iteration barrier (-1 = none)
 };
 
 constexpr int kTraceIters = 8;

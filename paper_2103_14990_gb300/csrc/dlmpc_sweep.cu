@@ -579,6 +579,10 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
     trace_point(P, iter, 3);
     __syncthreads();
     trace_point(P, iter, 4);
+    if (b == P.skip_arrival_cta) {  // test only: never arrive, the others' waits run out
+      ok = false;
+      break;
+    }
     unsigned my_nc = 0;
     if (tid == 0) {
       for (int t = 0; t < nli; ++t) {
