@@ -91,16 +91,17 @@ typedef struct {
   int32_t n_items;          /* column patches = n_sub_total */
   int32_t max_dcol, max_nullity;
   int64_t state_floats;     /* floats of one column-owned matrix (Phi, Psi or Lambda) */
-  int64_t operator_bytes;   /* bytes of all null-space bases N_j (FP32, padded) */
+  int64_t operator_bytes;   /* bytes of all null-space bases N_j and their transposes (FP32, padded) */
   int64_t offset_bytes;     /* bytes of all min-norm offsets q_c (FP32, padded) */
   int64_t exchange_floats;  /* floats of one row-partial-sum exchange buffer */
   int32_t grid_ctas, threads_per_cta, smem_bytes; /* launch of the ADMM sweep kernel */
   int32_t group_threads, groups_per_cta, wave; /* sweep shape (DLMPC_OPT_SWEEP_SHAPE) */
   int32_t resident_n_items;     /* patches whose N_j stays in shared memory for the whole step */
   int32_t resident_state_items; /* patches whose Psi, Lambda and q stay in shared memory */
-  int64_t iter_bytes;       /* algorithmic bytes of one ADMM iteration over all patches:
-                               N_j and q_c read, Psi/Lambda read+written, row partial
-                               sums read (|Patch(m)| per patch row) and written */
+  int64_t iter_bytes;       /* algorithmic bytes of one compact ADMM iteration over all
+                               patches: N_j and N_j^T read once each, row partial sums
+                               read (|Patch(m)| per patch row) and written, the compact
+                               iterate (lhat, R, Y) read and written */
 } dlmpc_info;
 
 /* Option keys for dlmpc_set_option. */
@@ -122,7 +123,14 @@ typedef struct {
                                           bounded wait runs out and the step returns
                                           DLMPC_ERR_TIMEOUT (-1 = off, the default) */
 #define DLMPC_OPT_RESIDENCY 8     /* shared-memory residency during a step: 0 none (all streamed),
-                                     1 Psi/Lambda/q, 2 (default) also N where it fits; replans */
+                                     1 compact iterate, Psi/Lambda and q, 2 (default) also N where
+                                     it fits; replans */
+#define DLMPC_OPT_COMPACT 13      /* != 0 (default): iterations after the first of a step carry the
+                                     projected iterate as Psi = q + N t and Lambda = x_c lhat (the
+                                     same iterates as Alg. 2, with the v = Psi + alpha x algebra of
+                                     Psi-comp done once per patch instead of once per column);
+                                     0: every iteration projects the stored Psi/Lambda.  Ignored
+                                     (full form) while DLMPC_OPT_EXPORT_PHI is on. */
 
 /* Builds the locality structure (hop-distance BFS, Patch(j), rows of Z_AB that
  * touch each patch) for n_inst instances, copies all inputs to the device and

@@ -40,6 +40,7 @@ OPT_TRACE = 9
 OPT_GRAPH = 10
 OPT_LEARN_PLANT = 11
 OPT_TEST_SKIP_ARRIVAL = 12
+OPT_COMPACT = 13
 
 # Every entry point declared in include/dlmpc.h (checked by the tests).
 EXPORTED = [

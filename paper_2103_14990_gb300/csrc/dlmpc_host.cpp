@@ -132,7 +132,8 @@ struct dlmpc_ctx {
   int grid = 0, gt = 128, ng = 4, wave = 2, grp_floats = 0, cta_floats = 0, max_local_inst = 1;
   size_t smem = 0;
   int64_t resident_n_items = 0, resident_state_items = 0;
-  int residency = 2;  // 0: nothing resident, 1: Psi/Lambda/q resident, 2: also N
+  int residency = 2;  // 0: nothing resident, 1: compact iterate, Psi/Lambda and q resident, 2: also N
+  int compact = 1;    // iterations after the first of a launch on the compact iterate
   int trace = 0;
   std::vector<int32_t> grp_ptr, grp_items, cta_inst_ptr, cta_inst;
   // options
@@ -144,7 +145,7 @@ struct dlmpc_ctx {
   DevBuf<int32_t> d_members, d_rev, d_np, d_grp_ptr, d_grp_items, d_cta_inst_ptr, d_cta_inst, d_adj_ptr, d_adj_idx,
       d_inst_iters, d_err, d_inst_item_ptr, d_sub_off;
   DevBuf<int64_t> d_goff;
-  DevBuf<float> d_N, d_q, d_psi, d_lam, d_phi, d_G0, d_G1, d_S, d_qw, d_rw, d_xlo, d_xhi, d_ulo, d_uhi, d_rho,
+  DevBuf<float> d_N, d_q, d_cp, d_psi, d_lam, d_phi, d_G0, d_G1, d_S, d_qw, d_rw, d_xlo, d_xhi, d_ulo, d_uhi, d_rho,
       d_epsp, d_epsd, d_item_r, d_item_s, d_x, d_u, d_xn;
   DevBuf<double> d_Adiag, d_Aoff, d_B;
   DevBuf<unsigned long long> d_bar, d_trace;
@@ -166,9 +167,10 @@ struct dlmpc_ctx {
     bool stats;
     int plan, fixed, max_iter;
     bool phi, trace;
+    int compact;
     bool operator==(const GraphKey &o) const {
       return x == o.x && u == o.u && xn == o.xn && warm == o.warm && stats == o.stats && plan == o.plan &&
-             fixed == o.fixed && max_iter == o.max_iter && phi == o.phi && trace == o.trace;
+             fixed == o.fixed && max_iter == o.max_iter && phi == o.phi && trace == o.trace && compact == o.compact;
     }
   };
   struct GraphEntry {
@@ -636,7 +638,7 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
   }
   int64_t max_n = 4;
   for (const Item &it : ctx->items) max_n = std::max<int64_t>(max_n, (int64_t)it.dred_pad * it.kpad);
-  const int cta_floats = 8 + 4 * ((2 * max_li + 3) / 4);
+  const int cta_floats = 8 + 4 * ((3 * max_li + 3) / 4);
   (void)max_n;  // N that is not resident is read from global memory directly
   int64_t used_max = 0;
   std::vector<std::vector<std::vector<int32_t>>> groups(grid);
@@ -659,26 +661,37 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
         for (auto &gl : groups[b])
           if (depth < gl.size()) { rr.push_back(gl[depth]); more = true; }
       }
+      // the compact iterate (touched every iteration), then N (read twice per
+      // iteration), then Psi/Lambda and q (first iteration and the ends of
+      // a launch, or every iteration when Phi is exported)
       for (int id : rr) {
         Item &it = ctx->items[id];
-        const int64_t need = 2LL * nx * it.r_sub * it.n_mem + (int64_t)nx * it.dred_pad;
-        it.n_sm = it.q_sm = it.st_sm = -1;
+        const int64_t need = cp_floats(it, nx);
+        it.n_sm = it.q_sm = it.st_sm = it.cp_sm = -1;
         if (ctx->residency >= 1 && used + need <= arena_cap) {
-          it.st_sm = (int32_t)used;
-          it.q_sm = (int32_t)(used + 2LL * nx * it.r_sub * it.n_mem);
+          it.cp_sm = (int32_t)used;
           used += need;
-          ++ctx->resident_state_items;
         }
       }
       for (int id : rr) {
         Item &it = ctx->items[id];
-        const int64_t need = (int64_t)it.dred_pad * it.kpad;
+        const int64_t need = (int64_t)it.dred_pad * it.kpad;  // N only: resident patches skip N^T
         if (ctx->residency >= 2 && used + need <= arena_cap) {
           it.n_sm = (int32_t)used;
           used += need;
           ++ctx->resident_n_items;
         } else {
           any_streamed = true;
+        }
+      }
+      for (int id : rr) {
+        Item &it = ctx->items[id];
+        const int64_t need = 2LL * nx * it.r_sub * it.n_mem + (int64_t)nx * it.dred_pad;
+        if (ctx->residency >= 1 && used + need <= arena_cap) {
+          it.st_sm = (int32_t)used;
+          it.q_sm = (int32_t)(used + 2LL * nx * it.r_sub * it.n_mem);
+          used += need;
+          ++ctx->resident_state_items;
         }
       }
       used_max = std::max(used_max, used);
@@ -818,11 +831,18 @@ extern "C" int dlmpc_precompute(dlmpc_ctx *ctx) {
     it.kpad = (int)round_up(std::max(it.k, 1), 4);
     if ((it.kpad / 4) % 2 == 0) it.kpad += 4;
     it.n_off = noff;
-    noff += round_up((int64_t)it.dred_pad * it.kpad, 4);
+    noff += round_up((int64_t)n_floats(it), 4);
     ctx->max_kpad = std::max(ctx->max_kpad, it.kpad);
     ctx->max_dred_pad = std::max(ctx->max_dred_pad, it.dred_pad);
   }
   ctx->n_floats = noff;
+  int64_t cpoff = 0;
+  for (Item &it : ctx->items) {
+    it.cp_off = cpoff;
+    it.cp_sm = -1;
+    cpoff += cp_floats(it, nx);
+  }
+  CK(ctx->d_cp.alloc(std::max<int64_t>(cpoff, 4)), "alloc compact iterates");
   CK(upload(ctx->d_items, ctx->items, s), "upload items");
   CK(ctx->d_N.alloc(noff), "alloc N");
   CK(launch_repack(d_scr.p, ctx->d_items.p, ctx->n_sub, d_Nscr.p, ctx->d_N.p, s), "repack_kernel");
@@ -938,6 +958,8 @@ Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_d
   P.max_local_inst = ctx->max_local_inst;
   P.trace = ctx->trace ? ctx->d_trace.p : nullptr;
   P.skip_arrival_cta = ctx->skip_arrival_cta;
+  P.compact = ctx->compact;
+  P.cpst = ctx->d_cp.p;
   return P;
 }
 
@@ -966,7 +988,7 @@ int enqueue_step(dlmpc_ctx *ctx, const Params &P, bool with_stats, bool events, 
 // pointers and options.
 int graph_step(dlmpc_ctx *ctx, const Params &P, bool with_stats) {
   dlmpc_ctx::GraphKey key{P.x, P.u, P.x_next, P.warm, with_stats, ctx->plan_version, P.fixed_iters, P.max_iter,
-                          P.Phi != nullptr, P.trace != nullptr};
+                          P.Phi != nullptr, P.trace != nullptr, P.compact};
   for (auto &ge : ctx->graphs)
     if (ge.key == key) {
       CK(cudaGraphLaunch(ge.exec, ctx->stream), "cudaGraphLaunch");
@@ -1229,6 +1251,7 @@ extern "C" int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value) {
     case DLMPC_OPT_GRAPH: ctx->use_graph = value != 0; return 0;
     case DLMPC_OPT_LEARN_PLANT: ctx->learn_plant = value != 0; return 0;
     case DLMPC_OPT_TEST_SKIP_ARRIVAL: ctx->skip_arrival_cta = (int)value; return 0;
+    case DLMPC_OPT_COMPACT: ctx->compact = value != 0; return 0;
     case DLMPC_OPT_RESIDENCY: {
       if (!(value >= 0 && value <= 2)) return ctx->fail(DLMPC_ERR_ARG, "residency must be 0, 1 or 2");
       ctx->residency = (int)value;
@@ -1268,14 +1291,16 @@ extern "C" int dlmpc_get_info(dlmpc_ctx *ctx, dlmpc_info *info) {
   info->wave = ctx->wave;
   info->resident_n_items = (int32_t)ctx->resident_n_items;
   info->resident_state_items = (int32_t)ctx->resident_state_items;
+  // bytes one compact iteration must move per patch: N_j and N_j^T read once
+  // each, the row sums of every patch row read, the patch's own row sums
+  // written, lhat and R read and written, Y read and written
   int64_t bytes = 0;
   for (const Item &it : ctx->items) {
     const int64_t dcol = (int64_t)it.r_sub * it.n_mem;
-    bytes += (int64_t)it.dred * it.k * 4;            // N_j
-    bytes += (int64_t)ctx->nx * it.dred * 4;         // q_c
-    bytes += 4LL * ctx->nx * dcol * 4;               // Psi, Lambda read and written
+    bytes += 2LL * it.dred * it.k * 4;               // N_j, N_j^T
     for (int e = 0; e < it.n_mem; ++e) bytes += (int64_t)ctx->np_of[ctx->members[it.mem_off + e]] * it.r_sub * 4;
     bytes += dcol * 4;                               // row partial sums written
+    bytes += 2LL * (dcol + it.dred + it.k) * 4;      // lhat, R, Y
   }
   info->iter_bytes = bytes;
   return 0;

@@ -1,5 +1,7 @@
 // Internal layout shared by the host setup and the CUDA kernels of the solver.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 namespace dlmpc {
@@ -22,7 +24,7 @@ struct Item {
   int32_t k;          // nullity of the restricted constraint
   int32_t kpad;       // odd row stride of N (>= k)
   int32_t mrows;      // kept constraint rows (reduced)
-  int64_t n_off;      // float offset of N: dred_pad x kpad, row-major
+  int64_t n_off;      // float offset of N (dred_pad x kpad) and N^T (k x dred_pad), row-major
   int64_t q_off;      // float offset of q: nx x dred_pad
   int64_t st_off;     // float offset of the column-owned state: nx x (r_sub * n_mem)
   int64_t z_off;      // offset into the reduced constraint CSR row pointer array
@@ -32,7 +34,23 @@ struct Item {
   int32_t q_sm;       // resident q (float offset), or -1: read from global memory
   int32_t st_sm;      // resident Psi then Lambda (2 * nx * D_col floats), or -1: global memory
   int32_t lslot;      // slot of the item's instance among the instances of its CTA
+  int64_t cp_off;     // float offset of the compact iterate (see cp_floats), global copy
+  int32_t cp_sm;      // resident compact iterate (float offset), or -1: global memory
+  int32_t cp_pad;
 };
+
+// Floats of the projection operator of one item: N (dred_pad x kpad) then
+// N^T (k x dred_pad), both row-major.
+inline __host__ __device__ unsigned n_floats(const Item &it) {
+  return (unsigned)(it.dred_pad * it.kpad + it.k * it.dred_pad);
+}
+
+// Compact iterate of one item (iterations after the first of a launch):
+// lhat [round4(D_col)] (reduced rows, then slot-0 rows), R [dred_pad],
+// Y [kpad], t0 [nx][kpad].
+inline __host__ __device__ int cp_floats(const Item &it, int nx) {
+  return ((it.r_sub * it.n_mem + 3) & ~3) + it.dred_pad + (1 + nx) * it.kpad;
+}
 
 // Arguments of the persistent ADMM sweep kernel.
 struct Params {
@@ -89,6 +107,8 @@ struct Params {
   unsigned long long *trace;  // optional [grid][kTraceIters][kTracePoints] globaltimer stamps
   int32_t skip_arrival_cta;   // test of the bounded waits: this CTA leaves before its first
                               // iteration barrier (-1 = none)
+  int32_t compact;            // != 0: iterations after the first use the compact iterate
+  float *cpst;                // compact iterates of the items without shared-memory residency
 };
 
 constexpr int kTraceIters = 8;

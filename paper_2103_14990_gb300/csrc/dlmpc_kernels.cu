@@ -4,7 +4,7 @@
 //                  constraint block -> null-space basis N_j, min-norm offsets q_c
 //                  (Alg. 1 "precompute necessities of closed-form solutions").
 //  repack_kernel   copies N_j from the bound-strided scratch into the packed
-//                  odd-stride layout read by the sweep.
+//                  odd-stride layout read by the sweep, followed by N_j^T.
 //  (the persistent ADMM sweep itself is in dlmpc_sweep.cu)
 //  stats_kernel    per-instance iteration count, status and residual maxima.
 #include <cuda_runtime.h>
@@ -236,6 +236,12 @@ __global__ void repack_kernel(const Item *scratch_items, const Item *items, int 
     float v = 0.f;
     if (row < d.dred && col < d.k) v = src[s.n_off + (int64_t)row * s.kpad + col];
     dst[d.n_off + e] = v;
+  }
+  // N^T after N: k rows of dred_pad
+  float *dt = dst + d.n_off + total;
+  for (int64_t e = threadIdx.x; e < (int64_t)d.k * d.dred_pad; e += blockDim.x) {
+    const int col = (int)(e / d.dred_pad), row = (int)(e % d.dred_pad);
+    dt[e] = row < d.dred ? src[s.n_off + (int64_t)row * s.kpad + col] : 0.f;
   }
 }
 

@@ -31,13 +31,21 @@
 namespace dlmpc {
 
 struct GroupLayout {
-  int alpha, vred, psired, t, part, red, mtab, icache, mbar, total;
+  int alpha, vred, psired, t, part, red, mtab, rtab, icache, mbar, total;
 };
 
 // Floats of one cached item: the Item, then rho, eps_p, eps_d, its own index.
 constexpr int kItemFloats = (int)((sizeof(Item) + 3) / 4) + 4;
 
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
+__host__ __device__ inline int max3(int a, int b, int c) { return a > b ? (a > c ? a : c) : (b > c ? b : c); }
+
+// Floats of one row record (reduced order: the reduced rows of the patch,
+// then its slot-0 rows): int exchange read offset, int |Patch(m)|, int
+// exchange write offset, int aux; den = rho / (rho + 2 q s), lo, hi, 1/s.
+// aux: u index (sub * nu + b) of an own slot-0 input row, own state index c of
+// an own slot-0 state row, otherwise -1.
+constexpr int kRowRecord = 8;
 
 // Floats of one patch-member record: exchange read offset, |Patch|, 1/s (0
 // when s = 0), exchange write base, then x[nx], rho/(rho + 2 q s)[nx],
@@ -53,9 +61,10 @@ __host__ __device__ inline GroupLayout group_layout(int nx, int nu, int gt, int 
   L.vred = o;   o += nx * max_dred_pad;
   L.psired = o; o += nx * max_dred_pad;
   L.t = o;      o += round4(nx * max_kpad);
-  L.part = o;   o += (gt / 32) * nx * max_kpad;
+  L.part = o;   o += round4(max3((gt / 32) * nx * max_kpad, 4 * gt, max_dred_pad));
   L.red = o;    o += round4(4 * (gt / 32));
   L.mtab = o;   o += round4(wave * max_nmem * member_record(nx, nu));
+  L.rtab = o;   o += wave * max_dcol * kRowRecord;
   L.icache = o; o += round4(wave * kItemFloats);
   L.mbar = o;   o += 4;
   L.total = o;
@@ -74,18 +83,19 @@ __device__ __forceinline__ void group_sync(int g, int gt_threads) {
 }
 
 struct Group {
-  float *alpha, *vred, *psired, *t, *part, *mtab, *icache;
+  float *alpha, *vred, *psired, *t, *part, *mtab, *rtab, *icache;
   double *red;
   uint64_t *mbar;
   unsigned phase;  // completed bulk copies on mbar
 };
 
-// Caches the wave's items (with their instance constants) and fills the
-// member records of their patches, so the iteration loop reads nothing but
-// the exchange sums (and non-resident N) from global memory.
+// Caches the wave's items (with their instance constants), fills the member
+// records of their patches and, from those, one record per patch row, so the
+// iteration loop reads nothing but the exchange sums (and non-resident N)
+// from global memory.
 template <int NX>
 __device__ __forceinline__ void fill_wave(const Params &P, const int *items, int wn, float *icache, float *mtab,
-                                          int gt, int GT) {
+                                          float *rtab, int g, int gt, int GT) {
   const int MT = member_record(NX, P.nu);
   constexpr int kItemWords = (int)((sizeof(Item) + 3) / 4);
   for (int e = gt; e < wn * kItemWords; e += GT) {
@@ -127,6 +137,49 @@ __device__ __forceinline__ void fill_wave(const Params &P, const int *items, int
       }
     }
   }
+  group_sync(g, GT);
+  for (int wi = 0; wi < wn; ++wi) {
+    const Item &it = P.items[items[wi]];
+    const float *tab = mtab + wi * P.max_nmem * MT;
+    float *rt = rtab + wi * P.max_dcol * kRowRecord;
+    const int r_sub = it.r_sub, rs_red = r_sub - NX, dred = it.dred, nxT = NX * it.T;
+    for (int p = gt; p < r_sub * it.n_mem; p += GT) {
+      int mpos, r;
+      if (p < dred) {
+        mpos = p / rs_red;
+        r = p - mpos * rs_red + NX;
+      } else {
+        mpos = (p - dred) / NX;
+        r = p - dred - mpos * NX;
+      }
+      const float *rec = tab + mpos * MT;
+      const bool own = mpos == it.self_pos;
+      int aux = -1;
+      float den, lo, hi;
+      if (r < nxT) {
+        const int a = r % NX;
+        den = rec[4 + NX + a];
+        lo = r >= NX ? rec[4 + 2 * NX + a] : -INFINITY;
+        hi = r >= NX ? rec[4 + 3 * NX + a] : INFINITY;
+        if (own && r < NX) aux = r;
+      } else {
+        const int bb = (r - nxT) % P.nu;
+        den = rec[4 + 4 * NX + bb];
+        lo = rec[4 + 4 * NX + P.nu + bb];
+        hi = rec[4 + 4 * NX + 2 * P.nu + bb];
+        if (own && r < nxT + P.nu) aux = it.sub * P.nu + bb;
+      }
+      int *ri = reinterpret_cast<int *>(rt + p * kRowRecord);
+      ri[0] = reinterpret_cast<const int *>(rec)[0] + r;
+      ri[1] = reinterpret_cast<const int *>(rec)[1];
+      ri[2] = reinterpret_cast<const int *>(rec)[3] + r;
+      ri[3] = aux;
+      rt[p * kRowRecord + 4] = den;
+      rt[p * kRowRecord + 5] = lo;
+      rt[p * kRowRecord + 6] = hi;
+      rt[p * kRowRecord + 7] = rec[2];
+    }
+  }
 }
 
 __device__ __forceinline__ const Item &cached_item(const float *icache, int wi) {
@@ -138,68 +191,156 @@ __device__ __forceinline__ const float *cached_extra(const float *icache, int wi
 
 // Phi-comp for every row of one patch (Sec. II-A row problem, closed form):
 // w = (Psi - Lambda)_r . x_hat from the exchange sums, z = clip(rho w / (rho +
-// 2 q s), lo, hi), alpha = (z - w) / s (0 when s = 0).
-template <int NX, int GT>
-__device__ __forceinline__ void phi_rows(const Params &P, const Item &it, const float *tab, const float *Gcur,
-                                         float *alpha_out, float rho, int gt) {
+// 2 q s), lo, hi), alpha = (z - w) / s (0 when s = 0).  The new Phi row is
+// Psi_r - Lambda_r + alpha x_hat; only alpha is stored.
+// Closed form of one row from its w and row record (see phi_rows).
+__device__ __forceinline__ void phi_row(const Params &P, int p, int dred, int aux, float4 c, float w,
+                                        float *alpha_out) {
+  // z* = rho w / (rho + 2 q s), clipped; alpha = (z - w) / s; s = 0 gives phi = v
+  float al = 0.f, z = w;
+  if (c.w > 0.f) {
+    z = fminf(fmaxf(w * c.x, c.y), c.z);
+    al = (z - w) * c.w;
+  }
+  alpha_out[p] = al;
+  if (aux >= 0 && p < dred) P.u[aux] = z;
+}
+
+// Phi-comp for every row of one patch (Sec. II-A row problem, closed form):
+// w = (Psi - Lambda)_r . x_hat from the exchange sums, z = clip(rho w / (rho +
+// 2 q s), lo, hi), alpha = (z - w) / s (0 when s = 0).  The new Phi row is
+// Psi_r - Lambda_r + alpha x_hat; only alpha is stored, in reduced order
+// (the reduced rows, then the slot-0 rows).  A thread takes two rows at a
+// time and issues the exchange loads of both before adding them.
+template <int GT>
+__device__ __forceinline__ void phi_rows(const Params &P, const Item &it, const float *rt, const float *Gcur,
+                                         float *alpha_out, int gt) {
   const int r_sub = it.r_sub;
   const int dcol = r_sub * it.n_mem;
-  const int nxT = NX * it.T;
-  const int MT = member_record(NX, P.nu);
-  const int dm = GT / r_sub, dr = GT - dm * r_sub;  // row stepping without division
-  int mpos = gt / r_sub, r = gt - mpos * r_sub;
-  for (int f = gt; f < dcol; f += GT) {
-    const float *rec = tab + mpos * MT;
-    const int goff = reinterpret_cast<const int *>(rec)[0];
-    const int np = reinterpret_cast<const int *>(rec)[1];
-    const float *gp = Gcur + goff + r;
-    // the exchange loads are independent: issue them together, add in slot order
-    float w = 0.f;
-    for (int s0 = 0; s0 < np; s0 += 8) {
-      float gv[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) gv[j] = (s0 + j < np) ? __ldcg(gp + (s0 + j) * r_sub) : 0.f;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) w += gv[j];
+  for (int p = gt; p < dcol; p += 2 * GT) {
+    const int p2 = p + GT;
+    const bool two = p2 < dcol;
+    const int4 ia = *reinterpret_cast<const int4 *>(rt + p * kRowRecord);
+    const float4 ca = *reinterpret_cast<const float4 *>(rt + p * kRowRecord + 4);
+    int4 ib = make_int4(0, 0, 0, -1);
+    float4 cb = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (two) {
+      ib = *reinterpret_cast<const int4 *>(rt + p2 * kRowRecord);
+      cb = *reinterpret_cast<const float4 *>(rt + p2 * kRowRecord + 4);
     }
-    const float inv_s = rec[2];
-    float den, lo, hi;
-    if (r < nxT) {
-      const int a = r % NX;
-      den = rec[4 + NX + a];
-      if (r >= NX) {
-        lo = rec[4 + 2 * NX + a];
-        hi = rec[4 + 3 * NX + a];
-      } else {
-        lo = -INFINITY;
-        hi = INFINITY;
+    const float *gp = Gcur + ia.x;
+    const float *gp2 = Gcur + ib.x;
+    float w = 0.f, w2 = 0.f;
+    for (int s0 = 0; s0 < max(ia.y, ib.y); s0 += 8) {
+      float gv[8], gv2[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        gv[j] = (s0 + j < ia.y) ? __ldcg(gp + (s0 + j) * r_sub) : 0.f;
+        gv2[j] = (s0 + j < ib.y) ? __ldcg(gp2 + (s0 + j) * r_sub) : 0.f;
       }
-    } else {
-      const int bb = (r - nxT) % P.nu;
-      den = rec[4 + 4 * NX + bb];
-      lo = rec[4 + 4 * NX + P.nu + bb];
-      hi = rec[4 + 4 * NX + 2 * P.nu + bb];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        w += gv[j];
+        w2 += gv2[j];
+      }
     }
-    // z* = rho w / (rho + 2 q s), clipped; alpha = (z - w) / s; s = 0 gives phi = v
-    float a = 0.f, z = w;
-    if (inv_s > 0.f) {
-      z = fminf(fmaxf(w * den, lo), hi);
-      a = (z - w) * inv_s;
-    }
-    alpha_out[f] = a;
-    if (mpos == it.self_pos && r >= nxT && r < nxT + P.nu) P.u[(int64_t)it.sub * P.nu + (r - nxT)] = z;
-    mpos += dm;
-    r += dr;
-    if (r >= r_sub) { r -= r_sub; ++mpos; }
+    phi_row(P, p, it.dred, ia.w, ca, w, alpha_out);
+    if (two) phi_row(P, p2, it.dred, ib.w, cb, w2, alpha_out);
   }
 }
 
-// Psi-comp, Lambda-comp and the residuals of one patch.
+// psi_red[c] = q_c + N t_c over the reduced rows, for every own column c (the
+// second half of Psi-comp).  16 consecutive rows per half warp (conflict-free
+// with an odd number of 16-byte units per row); the two halves of a warp cover
+// the two halves of the columns of the same rows.
+template <int NX, int GT>
+__device__ __forceinline__ void apply_n(const float *Nb, const float *tv, const float *q_p, int dred, int dred_pad,
+                                        int kpad, int ldr, float *out, int gt) {
+  constexpr int kWarps = GT / 32;
+  const int ncg = kpad >> 2;
+  const int lane = gt & 31, w = gt >> 5;
+  const int half = lane >> 4;
+  const int h0 = (ncg + 1) >> 1;
+  const int cg_begin = half ? h0 : 0, cg_end = half ? ncg : h0;
+  for (int base = w * 16; base < dred; base += kWarps * 16) {
+    const int red = base + (lane & 15);
+    float o[NX];
+#pragma unroll
+    for (int c = 0; c < NX; ++c) o[c] = 0.f;
+    if (red < dred) {
+      const float *nrow = Nb + red * kpad;
+      for (int cg0 = cg_begin; cg0 < cg_end; cg0 += 4) {
+        float4 n4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          n4[u] = (cg0 + u < cg_end) ? *reinterpret_cast<const float4 *>(nrow + 4 * (cg0 + u))
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (cg0 + u < cg_end) {
+#pragma unroll
+            for (int c = 0; c < NX; ++c) {
+              const float4 t4 = *reinterpret_cast<const float4 *>(tv + c * kpad + 4 * (cg0 + u));
+              o[c] = fmaf(n4[u].x, t4.x, o[c]);
+              o[c] = fmaf(n4[u].y, t4.y, o[c]);
+              o[c] = fmaf(n4[u].z, t4.z, o[c]);
+              o[c] = fmaf(n4[u].w, t4.w, o[c]);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NX; ++c) o[c] += __shfl_xor_sync(0xffffffffu, o[c], 16);
+    if (red < dred && half == 0) {
+#pragma unroll
+      for (int c = 0; c < NX; ++c) out[c * ldr + red] = o[c] + q_p[c * dred_pad + red];
+    }
+  }
+}
+
+// Conv of one patch from the per-thread squared residual partials (Sec. II-A
+// stopping rule, per subsystem): ||Phi - Psi||_F <= eps_p and
+// rho ||Psi - Psi_prev||_F <= eps_d.  GB300 runs FP64 at a small fraction of
+// FP32: sums of a few squares stay in FP32 (tree order, relative error
+// ~1e-6), the per-warp sums are combined in FP64 and squared residuals are
+// compared (no square root on the path).
+template <int GT>
+__device__ __forceinline__ void finish_item(const Params &P, int idx, const Item &it, const float *extra, Group &G,
+                                            float prim_f, float dual_f, int g, int gt, unsigned *lnc, int iter) {
+  constexpr int kWarps = GT / 32;
+  const float prim_w = warp_sum_f(prim_f);
+  const float dual_w = warp_sum_f(dual_f);
+  if ((gt & 31) == 0) {
+    G.red[2 * (gt >> 5)] = (double)prim_w;
+    G.red[2 * (gt >> 5) + 1] = (double)dual_w;
+  }
+  group_sync(g, GT);
+  if (gt == 0) {
+    double pp = 0.0, dd = 0.0;
+    for (int w = 0; w < kWarps; ++w) {
+      pp += G.red[2 * w];
+      dd += G.red[2 * w + 1];
+    }
+    const double rho = extra[0], epsp = extra[1], epsd = extra[2];
+    const bool conv = pp <= epsp * epsp && rho * rho * dd <= epsd * epsd;
+    const float rj = sqrtf((float)pp);
+    const float sj = (float)rho * sqrtf((float)dd);
+    P.item_r[idx] = rj;
+    P.item_s[idx] = sj;
+    if (!(isfinite(rj) && isfinite(sj))) set_error(P.err, DLMPC_ERR_NONFINITE, blockIdx.x, iter, it.sub);
+    if (!conv) atomicAdd(lnc + it.lslot, 1u);
+  }
+}
+
+// Psi-comp, Lambda-comp and the residuals of one patch, from the stored Psi
+// and Lambda (the first iteration of a launch, and every iteration when Phi
+// is exported).  With `cp` set it also starts the compact iterate: t0 = t,
+// Y = 0, R = sum_c x_c Psi_c over the reduced rows.
 template <int NX, int GT>
 __device__ void project_item(const Params &P, int idx, const Item &it, const float *tab, const float *extra, Group &G,
                              const float *alpha, float *arena, float *Gnext, int g, int gt, unsigned *lnc, int iter,
-                             bool tr) {
-  const float rho = extra[0];
+                             float *cp, bool tr) {
   const int MT = member_record(NX, P.nu);
   const int r_sub = it.r_sub;
   const int dcol = r_sub * it.n_mem;
@@ -222,7 +363,7 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
     if (r >= r_sub) { r -= r_sub; ++mpos; }
     if (r >= NX) {
       const int red = mpos * rs_red + r - NX;
-      const float a = alpha[f];
+      const float a = alpha[red];
 #pragma unroll
       for (int c = 0; c < NX; ++c) G.vred[c * ldr + red] = psi_p[c * dcol + f] + a * xj[c];
     }
@@ -250,16 +391,16 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
         for (int c = 0; c < NX; ++c) acc[j][c] = 0.f;
       if (cg < ncg) {
         const float *nb = Nb + 4 * cg;
-        for (int r0 = 2 * w + hw; r0 < dred; r0 += 4 * kStep) {
+        for (int rb = 2 * w + hw; rb < dred; rb += 4 * kStep) {
           float4 n4[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int red = r0 + u * kStep;
+            const int red = rb + u * kStep;
             n4[u] = red < dred ? *reinterpret_cast<const float4 *>(nb + red * kpad) : make_float4(0.f, 0.f, 0.f, 0.f);
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int red = r0 + u * kStep;
+            const int red = rb + u * kStep;
             if (red < dred) {
 #pragma unroll
               for (int c = 0; c < NX; ++c) {
@@ -286,60 +427,24 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
     }
   }
   group_sync(g, GT);
+  const int cpl = (dcol + 3) & ~3;  // compact iterate: lhat, R, Y, t0
   for (int e = gt; e < NX * kpad; e += GT) {
     const int c = e / kpad, a = e - c * kpad;
     float s = 0.f;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) s += G.part[(w * NX + c) * kpad + a];
-    G.t[c * kpad + a] = (a < k) ? s : 0.f;  // padded columns of N are zero; keep t finite there
+    s = (a < k) ? s : 0.f;  // padded columns of N are zero; keep t finite there
+    G.t[c * kpad + a] = s;
+    if (cp) {
+      cp[cpl + it.dred_pad + kpad + e] = s;
+      if (c == 0) cp[cpl + it.dred_pad + a] = 0.f;
+    }
   }
   group_sync(g, GT);
   if (tr) trace_point(P, iter, 7);
 
-  // pass 2: psi_red = q + N t.  16 consecutive rows per half warp (conflict-
-  // free with an odd number of 16-byte units per row); the two halves of a
-  // warp cover the two halves of the columns of the same rows.
-  {
-    const int lane = gt & 31, w = gt >> 5;
-    const int half = lane >> 4;
-    const int h0 = (ncg + 1) >> 1;
-    const int cg_begin = half ? h0 : 0, cg_end = half ? ncg : h0;
-    for (int base = w * 16; base < dred; base += kWarps * 16) {
-      const int red = base + (lane & 15);
-      float o[NX];
-#pragma unroll
-      for (int c = 0; c < NX; ++c) o[c] = 0.f;
-      if (red < dred) {
-        const float *nrow = Nb + red * kpad;
-        for (int cg0 = cg_begin; cg0 < cg_end; cg0 += 4) {
-          float4 n4[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            n4[u] = (cg0 + u < cg_end) ? *reinterpret_cast<const float4 *>(nrow + 4 * (cg0 + u))
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (cg0 + u < cg_end) {
-#pragma unroll
-              for (int c = 0; c < NX; ++c) {
-                const float4 t4 = *reinterpret_cast<const float4 *>(G.t + c * kpad + 4 * (cg0 + u));
-                o[c] = fmaf(n4[u].x, t4.x, o[c]);
-                o[c] = fmaf(n4[u].y, t4.y, o[c]);
-                o[c] = fmaf(n4[u].z, t4.z, o[c]);
-                o[c] = fmaf(n4[u].w, t4.w, o[c]);
-              }
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < NX; ++c) o[c] += __shfl_xor_sync(0xffffffffu, o[c], 16);
-      if (red < dred && half == 0) {
-#pragma unroll
-        for (int c = 0; c < NX; ++c) G.psired[c * ldr + red] = o[c] + q_p[c * it.dred_pad + red];
-      }
-    }
-  }
+  // pass 2: psi_red = q + N t
+  apply_n<NX, GT>(Nb, G.t, q_p, dred, it.dred_pad, kpad, ldr, G.psired, gt);
   group_sync(g, GT);
 
   // slot-0 states pinned to e_c; Lambda-comp; residuals; new exchange sums
@@ -347,8 +452,8 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
   for (int f = gt, mpos = mpos0, r = r0; f < dcol; f += GT, mpos += dm, r += dr) {
     if (r >= r_sub) { r -= r_sub; ++mpos; }
     const int red = mpos * rs_red + r - NX;
-    const float a = alpha[f];
-    float gsum = 0.f;
+    const float a = alpha[r >= NX ? red : dred + mpos * NX + r];
+    float gsum = 0.f, rsum = 0.f;
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
       const float psi_old = psi_p[c * dcol + f];
@@ -364,35 +469,249 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
       lam_p[c * dcol + f] = lam_new;
       if (P.Phi) P.Phi[it.st_off + c * dcol + f] = lam_new - lam_old + ps;
       gsum = fmaf(2.f * ps - vv, xj[c], gsum);
+      rsum = fmaf(ps, xj[c], rsum);
     }
+    if (cp && r >= NX) cp[cpl + red] = rsum;
     Gnext[reinterpret_cast<const int *>(tab + mpos * MT)[3] + r] = gsum;
   }
-  // GB300 runs FP64 at a small fraction of FP32: sums of a few squares stay in
-  // FP32 (tree order, relative error ~1e-6), the per-warp sums are combined
-  // in FP64 and Conv compares squared residuals (no square root on the path).
-  const float prim_w = warp_sum_f(prim_f);
-  const float dual_w = warp_sum_f(dual_f);
-  if ((gt & 31) == 0) {
-    G.red[2 * (gt >> 5)] = (double)prim_w;
-    G.red[2 * (gt >> 5) + 1] = (double)dual_w;
+  finish_item<GT>(P, idx, it, extra, G, prim_f, dual_f, g, gt, lnc, iter);
+}
+
+// Psi-comp, Lambda-comp and Conv of one patch on the compact iterate (every
+// iteration after the first of a launch).  Once Psi_old = q + N t is a
+// projected iterate, N^T q = 0 and N^T N = I turn the projection of
+// v_c = Psi_old,c + alpha x_c into q_c + N (t_c + x_c y) with the single
+// vector y = N^T alpha (reduced rows).  With o = N y and s = ||x_j||^2:
+//   Psi_new,c - Psi_old,c = x_c o                (reduced rows; slot-0 rows fixed)
+//   Lambda_new,c = x_c lhat,  lhat = alpha - o   (reduced rows), alpha (slot-0 rows)
+//   R_new = R_old + s o,  R = sum_c x_c Psi_c over the reduced rows
+//   exchange sum of a row: sum_c x_c (Psi_new - Lambda_new)_c = R_new - s lhat
+//   ||Psi_new - Psi_old||^2 = s ||o||^2,  ||Lambda_new - Lambda_old||^2 = s ||lhat - lhat_old||^2
+// so an iteration reads N and N^T once each with one right-hand side and
+// touches neither Psi nor Lambda; Psi = q + N (t0 + x_c Y), Y = sum of the y,
+// and Lambda = x_c lhat are formed once at the end of the launch.  `first`:
+// Lambda_old is the stored Lambda of the first iteration, not yet of the form
+// x_c lhat.
+//
+// Both passes read their matrix flat: thread (q, g) owns the 16-byte column
+// group g of every QS-th row starting at row q, so a warp reads consecutive
+// 16-byte units, and the QS partial sums per output are added afterwards.
+template <int U>
+__device__ __forceinline__ void flat_pass(const float *M, int rows, int ld, const float *vec, float *part, int gt,
+                                          int GT) {
+  const int ng4 = ld >> 2;
+  const int QS = GT >= ng4 ? GT / ng4 : 1;
+  for (int e = gt; e < QS * ng4; e += GT) {  // one round unless ld > 4 GT
+    const int q = e / ng4, cg = e - q * ng4;
+    const float *mb = M + 4 * cg;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int rb = q; rb < rows; rb += U * QS) {
+      float4 m4[U];
+      float vv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int row = rb + u * QS;
+        const bool in = row < rows;
+        m4[u] = in ? *reinterpret_cast<const float4 *>(mb + row * ld) : make_float4(0.f, 0.f, 0.f, 0.f);
+        vv[u] = in ? vec[row] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        acc.x = fmaf(m4[u].x, vv[u], acc.x);
+        acc.y = fmaf(m4[u].y, vv[u], acc.y);
+        acc.z = fmaf(m4[u].z, vv[u], acc.z);
+        acc.w = fmaf(m4[u].w, vv[u], acc.w);
+      }
+    }
+    *reinterpret_cast<float4 *>(part + q * ld + 4 * cg) = acc;
+  }
+}
+
+// out[row] = M[row, :] . vec for a row-major M in shared memory whose row
+// stride has an odd number of 16-byte units: 16 consecutive rows per half
+// warp (conflict-free), the two halves of a warp splitting the columns.
+template <int GT>
+__device__ __forceinline__ void rows_pass(const float *M, int rows, int ld, const float *vec, float *out, int gt) {
+  constexpr int kWarps = GT / 32;
+  const int ncg = ld >> 2;
+  const int lane = gt & 31, w = gt >> 5, half = lane >> 4;
+  const int h0 = (ncg + 1) >> 1;
+  const int cg_begin = half ? h0 : 0, cg_end = half ? ncg : h0;
+  for (int base = w * 16; base < rows; base += kWarps * 16) {
+    const int row = base + (lane & 15);
+    float o = 0.f;
+    if (row < rows) {
+      const float *mrow = M + row * ld;
+      for (int cg0 = cg_begin; cg0 < cg_end; cg0 += 8) {
+        float4 m4[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          m4[u] = (cg0 + u < cg_end) ? *reinterpret_cast<const float4 *>(mrow + 4 * (cg0 + u))
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (cg0 + u < cg_end) {
+            const float4 v4 = *reinterpret_cast<const float4 *>(vec + 4 * (cg0 + u));
+            o = fmaf(m4[u].x, v4.x, o);
+            o = fmaf(m4[u].y, v4.y, o);
+            o = fmaf(m4[u].z, v4.z, o);
+            o = fmaf(m4[u].w, v4.w, o);
+          }
+        }
+      }
+    }
+    o += __shfl_xor_sync(0xffffffffu, o, 16);
+    if (row < rows && half == 0) out[row] = o;
+  }
+}
+
+template <int NX, int GT>
+__device__ void project_compact(const Params &P, int idx, const Item &it, const float *tab, const float *rt,
+                                const float *extra, Group &G, const float *alpha, float *arena, float *Gnext, int g,
+                                int gt, unsigned *lnc, int iter, bool first, bool tr) {
+  const int MT = member_record(NX, P.nu);
+  const int r_sub = it.r_sub;
+  const int dcol = r_sub * it.n_mem;
+  const int rs_red = r_sub - NX;
+  const int dred = it.dred, dpad = it.dred_pad;
+  const int k = it.k, kpad = it.kpad;
+  float *cp = it.cp_sm >= 0 ? arena + it.cp_sm : P.cpst + it.cp_off;
+  float *lhat = cp;
+  float *Rv = cp + ((dcol + 3) & ~3);
+  float *Y = Rv + dpad;
+  const float *lam_p = it.st_sm >= 0 ? arena + it.st_sm + NX * dcol : P.Lam + it.st_off;
+  const float *Nb = it.n_sm >= 0 ? arena + it.n_sm : P.Nmat + it.n_off;
+  const float *NTb = P.Nmat + it.n_off + dpad * kpad;  // N^T (k x dred_pad) follows N in global memory
+  float xj[NX];
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < NX; ++c) {
+    xj[c] = tab[it.self_pos * MT + 4 + c];
+    s = fmaf(xj[c], xj[c], s);
+  }
+  if (tr) trace_point(P, iter, 6);
+
+  // pass 1: y = N^T alpha_red; Y += y
+  flat_pass<8>(Nb, dred, kpad, alpha, G.part, gt, GT);
+  group_sync(g, GT);
+  {
+    const int ncg = kpad >> 2;
+    const int QS = GT >= ncg ? GT / ncg : 1;
+    for (int a = gt; a < kpad; a += GT) {
+      float y = 0.f;
+      if (a < k)
+        for (int q = 0; q < QS; ++q) y += G.part[q * kpad + a];
+      G.t[a] = y;
+      Y[a] += y;
+    }
   }
   group_sync(g, GT);
-  if (gt == 0) {
-    double pp = 0.0, dd = 0.0;
-    for (int w = 0; w < kWarps; ++w) {
-      pp += G.red[2 * w];
-      dd += G.red[2 * w + 1];
+  if (tr) trace_point(P, iter, 7);
+
+  // pass 2: o = N y, by rows of N where N is resident in shared memory,
+  // otherwise flat over N^T (whole 16-byte units from L2)
+  const bool resident = it.n_sm >= 0;
+  if (resident)
+    rows_pass<GT>(Nb, dred, kpad, G.t, G.part, gt);
+  else
+    flat_pass<8>(NTb, k, dpad, G.t, G.part, gt, GT);
+  group_sync(g, GT);
+
+  // Lambda-comp, residuals and exchange sums of the reduced rows
+  float prim_f = 0.f, dual_f = 0.f;
+  {
+    const int nrg = dpad >> 2;
+    const int QS = resident ? 1 : (GT >= nrg ? GT / nrg : 1);
+    for (int red = gt; red < dred; red += GT) {
+      float o = 0.f;
+      for (int q = 0; q < QS; ++q) o += G.part[q * dpad + red];
+      const float lh = alpha[red] - o;
+      if (first) {
+        const int mpos = red / rs_red, f = red + (mpos + 1) * NX;
+#pragma unroll
+        for (int c = 0; c < NX; ++c) {
+          const float dp = xj[c] * lh - lam_p[c * dcol + f];
+          prim_f = fmaf(dp, dp, prim_f);
+        }
+      } else {
+        const float dp = lh - lhat[red];
+        prim_f = fmaf(s * dp, dp, prim_f);
+      }
+      dual_f = fmaf(s * o, o, dual_f);
+      const float rn = fmaf(s, o, Rv[red]);
+      Rv[red] = rn;
+      lhat[red] = lh;
+      Gnext[reinterpret_cast<const int *>(rt + red * kRowRecord)[2]] = fmaf(-s, lh, rn);
     }
-    const double epsp = extra[1], epsd = extra[2];
-    const double rho2 = (double)rho * (double)rho;
-    const bool conv = pp <= epsp * epsp && rho2 * dd <= epsd * epsd;
-    const float rj = sqrtf((float)pp);
-    const float sj = rho * sqrtf((float)dd);
-    P.item_r[idx] = rj;
-    P.item_s[idx] = sj;
-    if (!(isfinite(rj) && isfinite(sj))) set_error(P.err, DLMPC_ERR_NONFINITE, blockIdx.x, iter, it.sub);
-    if (!conv) atomicAdd(lnc + it.lslot, 1u);
   }
+  // slot-0 rows: Psi fixed (e_c on the own member), lhat = alpha
+  for (int p = dred + gt; p < dcol; p += GT) {
+    const float a = alpha[p];
+    if (first) {
+      const int mpos = (p - dred) / NX, f = mpos * r_sub + (p - dred - mpos * NX);
+#pragma unroll
+      for (int c = 0; c < NX; ++c) {
+        const float dp = xj[c] * a - lam_p[c * dcol + f];
+        prim_f = fmaf(dp, dp, prim_f);
+      }
+    } else {
+      const float dp = a - lhat[p];
+      prim_f = fmaf(s * dp, dp, prim_f);
+    }
+    lhat[p] = a;
+    const int aux = reinterpret_cast<const int *>(rt + p * kRowRecord)[3];
+    float own = 0.f;
+#pragma unroll
+    for (int c = 0; c < NX; ++c)
+      if (aux == c) own = xj[c];
+    Gnext[reinterpret_cast<const int *>(rt + p * kRowRecord)[2]] = fmaf(-s, a, own);
+  }
+  finish_item<GT>(P, idx, it, extra, G, prim_f, dual_f, g, gt, lnc, iter);
+}
+
+// End of a launch whose last iteration ran on the compact iterate: Psi_c =
+// q_c + N (t0_c + x_c Y) (slot-0 rows e_c) and Lambda_c = x_c lhat, written
+// to the global state.
+template <int NX, int GT>
+__device__ void expand_compact(const Params &P, const Item &it, Group &G, float *arena, int g, int gt) {
+  const int r_sub = it.r_sub;
+  const int dcol = r_sub * it.n_mem;
+  const int rs_red = r_sub - NX;
+  const int dred = it.dred, k = it.k, kpad = it.kpad;
+  const int ldr = P.max_dred_pad;
+  const float *cp = it.cp_sm >= 0 ? arena + it.cp_sm : P.cpst + it.cp_off;
+  const float *lhat = cp;
+  const float *Y = cp + ((dcol + 3) & ~3) + it.dred_pad;
+  const float *t0 = Y + kpad;
+  const float *Nb = it.n_sm >= 0 ? arena + it.n_sm : P.Nmat + it.n_off;
+  const float *q_p = it.q_sm >= 0 ? arena + it.q_sm : P.qvec + it.q_off;
+  float xj[NX];
+#pragma unroll
+  for (int c = 0; c < NX; ++c) xj[c] = P.x[(int64_t)it.sub * NX + c];
+  for (int e = gt; e < NX * kpad; e += GT) {
+    const int c = e / kpad, a = e - c * kpad;
+    float xc = 0.f;
+#pragma unroll
+    for (int cc = 0; cc < NX; ++cc)
+      if (cc == c) xc = xj[cc];
+    G.t[e] = (a < k) ? fmaf(xc, Y[a], t0[e]) : 0.f;
+  }
+  group_sync(g, GT);
+  apply_n<NX, GT>(Nb, G.t, q_p, dred, it.dred_pad, kpad, ldr, G.psired, gt);
+  group_sync(g, GT);
+  for (int e = gt; e < NX * dcol; e += GT) {
+    const int c = e / dcol, f = e - c * dcol;
+    const int mpos = f / r_sub, r = f - mpos * r_sub;
+    const int red = mpos * rs_red + r - NX;
+    float xc = 0.f;
+#pragma unroll
+    for (int cc = 0; cc < NX; ++cc)
+      if (cc == c) xc = xj[cc];
+    const float ps = (r < NX) ? ((mpos == it.self_pos && r == c) ? 1.f : 0.f) : G.psired[c * ldr + red];
+    P.Psi[it.st_off + e] = ps;
+    P.Lam[it.st_off + e] = xc * lhat[r >= NX ? red : dred + mpos * NX + r];
+  }
+  group_sync(g, GT);
 }
 
 __device__ __forceinline__ void red_add_release_u64(unsigned long long *p, unsigned long long v) {
@@ -453,6 +772,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
   G.part = gbase + L.part;
   G.red = reinterpret_cast<double *>(gbase + L.red);
   G.mtab = gbase + L.mtab;
+  G.rtab = gbase + L.rtab;
   G.icache = gbase + L.icache;
   G.mbar = reinterpret_cast<uint64_t *>(gbase + L.mbar);
   G.phase = 0;
@@ -460,6 +780,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
   unsigned long long *prev_hi = reinterpret_cast<unsigned long long *>(cta);  // [3] (+1 pad)
   unsigned *lnc = reinterpret_cast<unsigned *>(cta + 8);                      // [max_local_inst]
   int *lact = reinterpret_cast<int *>(cta + 8 + P.max_local_inst);            // [max_local_inst]
+  int *lcnt = reinterpret_cast<int *>(cta + 8 + 2 * P.max_local_inst);        // [max_local_inst] iterations run
   float *arena = cta + P.cta_floats;
 
   const int gi0 = P.grp_ptr[b * P.ng + g];
@@ -469,6 +790,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
 
   if (gt == 0) mbar_init(G.mbar, 1);
   if (tid < 3) prev_hi[tid] = 0ull;
+  for (int t = tid; t < nli; t += blockDim.x) lcnt[t] = 0;
   __syncthreads();
 
   // ---- prologue: s_i, starting state, resident data, starting exchange sums
@@ -527,13 +849,14 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
   ok = sweep_barrier(P, e_bar++, 0u, prev_hi, total, -1);
   // s_m of every member is now visible: single-wave groups fill their tables once
   if (ok && one_wave && gi1 > gi0) {
-    fill_wave<NX>(P, P.grp_items + gi0, gi1 - gi0, G.icache, G.mtab, gt, GT);
+    fill_wave<NX>(P, P.grp_items + gi0, gi1 - gi0, G.icache, G.mtab, G.rtab, g, gt, GT);
     group_sync(g, GT);
   }
 
   // ---- ADMM iterations (Alg. 2)
   const int n_it = P.fixed_iters > 0 ? P.fixed_iters : P.max_iter;
   const bool multi = P.n_inst > 1;
+  const bool compact = P.compact != 0 && P.Phi == nullptr;
   const int MT = member_record(NX, P.nu);
   int iter = 0;
   for (; ok && iter < n_it; ++iter) {
@@ -546,6 +869,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
       if (multi && P.fixed_iters <= 0 && iter > 0)
         active = ld_acquire_u32(P.notconv + prev * P.n_inst + P.cta_inst[li0 + t]) > 0u;
       lact[t] = active;
+      lcnt[t] += active;
     }
     __syncthreads();
     trace_point(P, iter, 0);
@@ -555,14 +879,13 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
       const int wn = min(P.wave, gi1 - w0);
       if (!one_wave) {
         group_sync(g, GT);  // the previous wave is done with the cache
-        fill_wave<NX>(P, P.grp_items + w0, wn, G.icache, G.mtab, gt, GT);
+        fill_wave<NX>(P, P.grp_items + w0, wn, G.icache, G.mtab, G.rtab, g, gt, GT);
         group_sync(g, GT);
       }
       for (int wi = 0; wi < wn; ++wi) {
         const Item &it = cached_item(G.icache, wi);
         if (!lact[it.lslot]) continue;
-        phi_rows<NX, GT>(P, it, G.mtab + wi * P.max_nmem * MT, Gcur, G.alpha + wi * P.max_dcol,
-                         cached_extra(G.icache, wi)[0], gt);
+        phi_rows<GT>(P, it, G.rtab + wi * P.max_dcol * kRowRecord, Gcur, G.alpha + wi * P.max_dcol, gt);
       }
       group_sync(g, GT);
       if (w0 == gi0) trace_point(P, iter, 1);
@@ -570,8 +893,16 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
         const Item &it = cached_item(G.icache, wi);
         if (!lact[it.lslot]) continue;
         const float *ex = cached_extra(G.icache, wi);
-        project_item<NX, GT>(P, reinterpret_cast<const int *>(ex)[3], it, G.mtab + wi * P.max_nmem * MT, ex, G,
-                             G.alpha + wi * P.max_dcol, arena, Gnext, g, gt, lnc, iter, w0 == gi0 && wi == 0);
+        const int idx = reinterpret_cast<const int *>(ex)[3];
+        const bool tr = w0 == gi0 && wi == 0;
+        if (compact && iter > 0)
+          project_compact<NX, GT>(P, idx, it, G.mtab + wi * P.max_nmem * MT, G.rtab + wi * P.max_dcol * kRowRecord,
+                                  ex, G, G.alpha + wi * P.max_dcol, arena,
+                                  Gnext, g, gt, lnc, iter, iter == 1, tr);
+        else
+          project_item<NX, GT>(P, idx, it, G.mtab + wi * P.max_nmem * MT, ex, G, G.alpha + wi * P.max_dcol, arena,
+                               Gnext, g, gt, lnc, iter,
+                               compact ? (it.cp_sm >= 0 ? arena + it.cp_sm : P.cpst + it.cp_off) : nullptr, tr);
         if (w0 == gi0 && wi == 0) trace_point(P, iter, 2);
       }
       group_sync(g, GT);
@@ -605,10 +936,15 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
   }
   if (b == 0 && tid == 0) P.err[4] = iter;
 
-  // ---- epilogue: write back resident state, dynamics
+  // ---- epilogue: final Psi/Lambda (from the compact iterate, or the resident
+  // state written back), dynamics
   __syncthreads();
   for (int ii = gi0; ii < gi1; ++ii) {
     const Item &it = P.items[P.grp_items[ii]];
+    if (compact && lcnt[it.lslot] >= 2) {
+      expand_compact<NX, GT>(P, it, G, arena, g, gt);
+      continue;
+    }
     if (it.st_sm < 0) continue;
     const int n2 = 2 * NX * it.r_sub * it.n_mem;
     const int half = n2 / 2;

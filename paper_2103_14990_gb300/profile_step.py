@@ -1,0 +1,71 @@
+"""Runs a few MPC steps of one workload with a fixed sweep launch, for
+profilers (ncu) and phase traces.
+
+    python -m paper_2103_14990_gb300.profile_step --workload chain1024 \
+        --iters 50 --shape 1280701 --residency 2 --steps 3 [--trace]
+
+--shape is threads per group * 10000 + groups per CTA * 100 + wave (0 keeps
+the default plan); --iters runs exactly that many ADMM iterations per step
+from a cold start.  Prints the plan, the kernel time of every step and, with
+--trace, the median phase durations of the sweep over the CTAs.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+
+import numpy as np
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="chain1024", choices=["chain1024", "chain10", "grid64"])
+    ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--shape", type=int, default=0)
+    ap.add_argument("--residency", type=int, default=-1)
+    ap.add_argument("--compact", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--trace", action="store_true")
+    a = ap.parse_args(argv)
+    import torch
+    import paper_2103_14990_gb300 as pkg
+    from paper_2103_14990_gb300 import instances as I
+    p = {"chain1024": I.chain1024, "chain10": I.chain10, "grid64": I.grid64}[a.workload]()
+    s = pkg.Solver([p])
+    if a.residency >= 0:
+        s.set_option(pkg.OPT_RESIDENCY, a.residency)
+    if a.shape > 0:
+        s.set_option(pkg.OPT_SWEEP_SHAPE, a.shape)
+    s.set_option(pkg.OPT_COMPACT, a.compact)
+    s.set_option(pkg.OPT_FIXED_ITERS, a.iters)
+    s.set_option(pkg.OPT_TIMING, 1)
+    if a.trace:
+        s.set_option(pkg.OPT_TRACE, 1)
+    info = s.info()
+    print(json.dumps({k: info[k] for k in ("grid_ctas", "threads_per_cta", "group_threads", "groups_per_cta", "wave",
+                                           "smem_bytes", "resident_n_items", "resident_state_items")}))
+    x = torch.tensor(p.x0.astype(np.float32), device="cuda")
+    u = torch.zeros(p.n_sub, p.nu, device="cuda")
+    xn = torch.zeros_like(x)
+    for _ in range(a.steps):
+        rc, st = s.step(x, u, xn, warm=pkg.WARM_COLD)
+        ms = s.timing()[0]
+        print(f"kernel {ms:.4f} ms  {1e3 * ms / a.iters:.2f} us/iteration  status {st[0]['status']}")
+    if a.trace:
+        tr = s.trace().astype(np.int64)
+        names = ["phi", "pre", "pass1", "pass2+final", "rest", "cta_sync", "barrier"]
+        pts = [(0, 1), (1, 6), (6, 7), (7, 2), (2, 3), (3, 4), (4, 5)]
+        for it in range(1, tr.shape[1] - 1):
+            ok = tr[:, it, 0] > 0
+            row = [np.median((tr[ok, it, b] - tr[ok, it, a_]) / 1e3) for a_, b in pts]
+            arr = (tr[ok, it, 4] - tr[ok, it, 0]) / 1e3
+            tot = np.median((tr[ok, it + 1, 0] - tr[ok, it, 0]) / 1e3)
+            print(f"iter {it}: " + " ".join(f"{n} {v:.2f}" for n, v in zip(names, row)) +
+                  f" | arrival median {np.median(arr):.2f} max {np.max(arr):.2f} | total {tot:.2f} us")
+    s.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

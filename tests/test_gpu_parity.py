@@ -38,19 +38,22 @@ def gpu_solver(probs, torch):
     return pkg.Solver(probs)
 
 
-def run_fixed(solver, torch, x0, K, warm=0):
+def run_fixed(solver, torch, x0, K, warm=0, export=True):
+    """K iterations from `warm`; with export=False the step runs on the
+    compact iterate after its first iteration and phi comes back as None."""
     import paper_2103_14990_gb300 as pkg
     solver.set_option(pkg.OPT_FIXED_ITERS, K)
-    solver.set_option(pkg.OPT_EXPORT_PHI, 1)
+    solver.set_option(pkg.OPT_EXPORT_PHI, 1 if export else 0)
     x = torch.tensor(np.asarray(x0, np.float32).reshape(-1, solver.nx), device="cuda")
     u = torch.zeros(solver.n_sub, solver.nu, device="cuda")
     xn = torch.zeros_like(x)
     rc, st = solver.step(x, u, xn, warm=warm)
-    phi, psi, lam = solver.get_state(phi=True)
+    phi, psi, lam = solver.get_state(phi=export)
     torch.cuda.synchronize()
     solver.set_option(pkg.OPT_FIXED_ITERS, 0)
-    return (rc, st, phi.cpu().numpy(), psi.cpu().numpy(), lam.cpu().numpy(), u.cpu().numpy(),
-            xn.cpu().numpy())
+    solver.set_option(pkg.OPT_EXPORT_PHI, 0)
+    return (rc, st, phi.cpu().numpy() if export else None, psi.cpu().numpy(), lam.cpu().numpy(),
+            u.cpu().numpy(), xn.cpu().numpy())
 
 
 SMALL = {
@@ -92,6 +95,41 @@ def test_fixed_iterations_parity(name, K, torch):
     assert rel(u, u_ref) <= REL or np.max(np.abs(u - u_ref)) < 1e-7
     xn_ref = o.dynamics(p.x0, u)  # dynamics of the GPU's own u, FP64
     assert np.max(np.abs(xn.reshape(-1) - xn_ref.reshape(-1))) < 1e-6
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+@pytest.mark.parametrize("K", [1, 2, 3, 60])
+def test_fixed_iterations_parity_compact(name, K, torch):
+    """Iterations after the first on the compact iterate (Psi = q + N t,
+    Lambda = x_c lhat), expanded at the end of the step: Psi, Lambda and u
+    against the oracle, and against the full form of the same step."""
+    import paper_2103_14990_gb300 as pkg
+    p = SMALL[name]()
+    o = O.Oracle(p)
+    ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=K)
+    s = gpu_solver([p], torch)
+    rc, st, _, psi, lam, u, xn = run_fixed(s, torch, p.x0, K, export=False)
+    assert st[0]["iters"] == K
+    assert rel(psi, ref.Psi) <= REL
+    assert rel(lam, ref.Lam) <= REL or np.linalg.norm(ref.Lam) < 1e-6
+    u_ref = o.control(ref)
+    assert rel(u, u_ref) <= REL or np.max(np.abs(u - u_ref)) < 1e-7
+    s.set_option(pkg.OPT_COMPACT, 0)
+    rc, st_f, _, psi_f, lam_f, u_f, _ = run_fixed(s, torch, p.x0, K, export=False)
+    assert rel(psi, psi_f) <= 2e-5
+    assert rel(u, u_f) <= 2e-5 or np.max(np.abs(u - u_f)) < 1e-7
+    # residuals of the last iteration agree between the two forms
+    # (absolute floor: FP32 rounding of Lambda and Psi themselves)
+    scale = 1e-6 * max(np.linalg.norm(lam_f), np.linalg.norm(psi_f))
+    assert abs(st[0]["r_max"] - st_f[0]["r_max"]) <= 1e-3 * st_f[0]["r_max"] + scale
+    assert abs(st[0]["s_max"] - st_f[0]["s_max"]) <= 1e-3 * st_f[0]["s_max"] + scale
+    # warm continuation from the expanded state
+    s.set_option(pkg.OPT_COMPACT, 1)
+    rc, st2, _, psi2, lam2, u2, _ = run_fixed(s, torch, p.x0, K, warm=pkg.WARM_PREVIOUS, export=False)
+    ref2 = O.admm(o.lay, o.blocks, p.x0, Psi0=psi.astype(np.float64), Lam0=lam.astype(np.float64), fixed_iters=K)
+    assert rel(psi2, ref2.Psi) <= REL
+    assert rel(lam2, ref2.Lam) <= REL or np.linalg.norm(ref2.Lam) < 1e-6
     s.close()
 
 
@@ -182,8 +220,8 @@ def test_max_iter_status(torch):
     s.close()
 
 
-SHAPES = [(128, 4, 2, 2), (128, 4, 1, 0), (64, 8, 3, 1), (256, 2, 2, 0), (128, 1, 1, 2), (64, 2, 4, 0),
-          (64, 15, 2, 1)]
+SHAPES = [(128, 4, 2, 2), (128, 4, 1, 0), (64, 4, 3, 1), (256, 2, 2, 0), (128, 1, 1, 2), (64, 2, 4, 0),
+          (64, 15, 1, 1)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -213,6 +251,11 @@ def test_sweep_shapes_and_streaming(name, shape, torch):
     rc, st2, phi2, psi2, lam2, u2, xn2 = run_fixed(s, torch, p.x0, K, warm=pkg.WARM_PREVIOUS)
     ref2 = O.admm(o.lay, o.blocks, p.x0, Psi0=ref.Psi, Lam0=ref.Lam, fixed_iters=K)
     assert rel(psi2, ref2.Psi) <= REL
+    # the compact iterate (resident or in global memory) on the same shape
+    rc, st3, _, psi3, lam3, u3, _ = run_fixed(s, torch, p.x0, K, export=False)
+    assert rel(psi3, ref.Psi) <= REL
+    assert rel(lam3, ref.Lam) <= REL
+    assert rel(u3, o.control(ref)) <= REL or np.max(np.abs(u3 - o.control(ref))) < 1e-7
     s.close()
 
 
