@@ -503,17 +503,38 @@ __device__ __forceinline__ void flat_pass(const float *M, int rows, int ld, cons
   const int QS = GT >= ng4 ? GT / ng4 : 1;
   for (int e = gt; e < QS * ng4; e += GT) {  // one round unless ld > 4 GT
     const int q = e / ng4, cg = e - q * ng4;
-    const float *mb = M + 4 * cg;
+    const float *mp = M + q * ld + 4 * cg;
+    const float *vp = vec + q;
+    const int step = QS * ld;
+    int left = rows > q ? (rows - q + QS - 1) / QS : 0;  // rows of this thread
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int rb = q; rb < rows; rb += U * QS) {
+    // whole chunks of U rows without predicates (running pointers), then
+    // one predicated tail chunk
+    for (; left >= U; left -= U) {
       float4 m4[U];
       float vv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int row = rb + u * QS;
-        const bool in = row < rows;
-        m4[u] = in ? *reinterpret_cast<const float4 *>(mb + row * ld) : make_float4(0.f, 0.f, 0.f, 0.f);
-        vv[u] = in ? vec[row] : 0.f;
+        m4[u] = *reinterpret_cast<const float4 *>(mp + u * step);
+        vv[u] = vp[u * QS];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        acc.x = fmaf(m4[u].x, vv[u], acc.x);
+        acc.y = fmaf(m4[u].y, vv[u], acc.y);
+        acc.z = fmaf(m4[u].z, vv[u], acc.z);
+        acc.w = fmaf(m4[u].w, vv[u], acc.w);
+      }
+      mp += U * step;
+      vp += U * QS;
+    }
+    if (left > 0) {
+      float4 m4[U];
+      float vv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        m4[u] = u < left ? *reinterpret_cast<const float4 *>(mp + u * step) : make_float4(0.f, 0.f, 0.f, 0.f);
+        vv[u] = u < left ? vp[u * QS] : 0.f;
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -524,44 +545,6 @@ __device__ __forceinline__ void flat_pass(const float *M, int rows, int ld, cons
       }
     }
     *reinterpret_cast<float4 *>(part + q * ld + 4 * cg) = acc;
-  }
-}
-
-// out[row] = M[row, :] . vec for a row-major M in shared memory whose row
-// stride has an odd number of 16-byte units: 16 consecutive rows per half
-// warp (conflict-free), the two halves of a warp splitting the columns.
-template <int GT>
-__device__ __forceinline__ void rows_pass(const float *M, int rows, int ld, const float *vec, float *out, int gt) {
-  constexpr int kWarps = GT / 32;
-  const int ncg = ld >> 2;
-  const int lane = gt & 31, w = gt >> 5, half = lane >> 4;
-  const int h0 = (ncg + 1) >> 1;
-  const int cg_begin = half ? h0 : 0, cg_end = half ? ncg : h0;
-  for (int base = w * 16; base < rows; base += kWarps * 16) {
-    const int row = base + (lane & 15);
-    float o = 0.f;
-    if (row < rows) {
-      const float *mrow = M + row * ld;
-      for (int cg0 = cg_begin; cg0 < cg_end; cg0 += 8) {
-        float4 m4[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          m4[u] = (cg0 + u < cg_end) ? *reinterpret_cast<const float4 *>(mrow + 4 * (cg0 + u))
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (cg0 + u < cg_end) {
-            const float4 v4 = *reinterpret_cast<const float4 *>(vec + 4 * (cg0 + u));
-            o = fmaf(m4[u].x, v4.x, o);
-            o = fmaf(m4[u].y, v4.y, o);
-            o = fmaf(m4[u].z, v4.z, o);
-            o = fmaf(m4[u].w, v4.w, o);
-          }
-        }
-      }
-    }
-    o += __shfl_xor_sync(0xffffffffu, o, 16);
-    if (row < rows && half == 0) out[row] = o;
   }
 }
 
@@ -608,20 +591,15 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
   group_sync(g, GT);
   if (tr) trace_point(P, iter, 7);
 
-  // pass 2: o = N y, by rows of N where N is resident in shared memory,
-  // otherwise flat over N^T (whole 16-byte units from L2)
-  const bool resident = it.n_sm >= 0;
-  if (resident)
-    rows_pass<GT>(Nb, dred, kpad, G.t, G.part, gt);
-  else
-    flat_pass<8>(NTb, k, dpad, G.t, G.part, gt, GT);
+  // pass 2: o = N y, flat over N^T (from L2 also for patches whose N is resident)
+  flat_pass<8>(NTb, k, dpad, G.t, G.part, gt, GT);
   group_sync(g, GT);
 
   // Lambda-comp, residuals and exchange sums of the reduced rows
   float prim_f = 0.f, dual_f = 0.f;
   {
     const int nrg = dpad >> 2;
-    const int QS = resident ? 1 : (GT >= nrg ? GT / nrg : 1);
+    const int QS = GT >= nrg ? GT / nrg : 1;
     for (int red = gt; red < dred; red += GT) {
       float o = 0.f;
       for (int q = 0; q < QS; ++q) o += G.part[q * dpad + red];
@@ -734,8 +712,11 @@ __device__ __forceinline__ bool sweep_barrier(const Params &P, unsigned e, unsig
     int ok = 1;
     unsigned long long v = 0;
     for (unsigned spins = 0;; ++spins) {
-      v = ld_acquire_u64(ctr);
-      if ((unsigned)(v & 0xffffffffull) >= target) break;
+      v = ld_relaxed_u64(ctr);
+      if ((unsigned)(v & 0xffffffffull) >= target) {
+        fence_acquire();
+        break;
+      }
       if ((spins & 63u) == 63u) {
         if (ld_volatile_i32(P.err) != 0) { ok = 0; break; }
         if (global_ns() - t0 > P.timeout_ns) {
@@ -867,7 +848,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
       lnc[t] = 0u;
       int active = 1;
       if (multi && P.fixed_iters <= 0 && iter > 0)
-        active = ld_acquire_u32(P.notconv + prev * P.n_inst + P.cta_inst[li0 + t]) > 0u;
+        active = __ldcg(P.notconv + prev * P.n_inst + P.cta_inst[li0 + t]) > 0u;
       lact[t] = active;
       lcnt[t] += active;
     }
@@ -927,7 +908,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
     if (b == 0) {
       if (multi) {
         for (int e = tid; e < P.n_inst; e += blockDim.x)
-          if (P.inst_iters[e] == 0 && ld_acquire_u32(P.notconv + slot * P.n_inst + e) == 0u) P.inst_iters[e] = iter + 1;
+          if (P.inst_iters[e] == 0 && __ldcg(P.notconv + slot * P.n_inst + e) == 0u) P.inst_iters[e] = iter + 1;
       } else if (tid == 0 && total == 0u && P.inst_iters[0] == 0) {
         P.inst_iters[0] = iter + 1;
       }
