@@ -316,12 +316,16 @@ __device__ __forceinline__ void finish_item(const Params &P, int idx, const Item
     G.red[2 * (gt >> 5) + 1] = (double)dual_w;
   }
   group_sync(g, GT);
-  if (gt == 0) {
-    double pp = 0.0, dd = 0.0;
-    for (int w = 0; w < kWarps; ++w) {
-      pp += G.red[2 * w];
-      dd += G.red[2 * w + 1];
+  if (gt < 32) {
+    // lane w < kWarps holds warp w's sums; FP64 tree over the lanes
+    double pp = gt < kWarps ? G.red[2 * gt] : 0.0;
+    double dd = gt < kWarps ? G.red[2 * gt + 1] : 0.0;
+#pragma unroll
+    for (int o = kWarps / 2; o > 0; o >>= 1) {
+      pp += __shfl_xor_sync(0xffffffffu, pp, o);
+      dd += __shfl_xor_sync(0xffffffffu, dd, o);
     }
+    if (gt != 0) return;
     const double rho = extra[0], epsp = extra[1], epsd = extra[2];
     const bool conv = pp <= epsp * epsp && rho * rho * dd <= epsd * epsd;
     const float rj = sqrtf((float)pp);
@@ -372,7 +376,6 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
   // generic 16-byte loads below serve both.
   const float *Nb = it.n_sm >= 0 ? arena + it.n_sm : P.Nmat + it.n_off;
   group_sync(g, GT);
-  if (tr) trace_point(P, iter, 6);
 
   // pass 1: t = N^T v.  Warp w takes row pairs (2i, 2i+1), i = w mod kWarps;
   // the half warp picks the row, the lane a group of 4 columns (blocks of 16
@@ -446,6 +449,7 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
   // pass 2: psi_red = q + N t
   apply_n<NX, GT>(Nb, G.t, q_p, dred, it.dred_pad, kpad, ldr, G.psired, gt);
   group_sync(g, GT);
+  if (tr) trace_point(P, iter, 6);
 
   // slot-0 states pinned to e_c; Lambda-comp; residuals; new exchange sums
   float prim_f = 0.f, dual_f = 0.f;  // FP32 partials per thread and warp, combined in FP64
@@ -572,7 +576,6 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
     xj[c] = tab[it.self_pos * MT + 4 + c];
     s = fmaf(xj[c], xj[c], s);
   }
-  if (tr) trace_point(P, iter, 6);
 
   // pass 1: y = N^T alpha_red; Y += y
   flat_pass<8>(Nb, dred, kpad, alpha, G.part, gt, GT);
@@ -594,6 +597,7 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
   // pass 2: o = N y, flat over N^T (from L2 also for patches whose N is resident)
   flat_pass<8>(NTb, k, dpad, G.t, G.part, gt, GT);
   group_sync(g, GT);
+  if (tr) trace_point(P, iter, 6);
 
   // Lambda-comp, residuals and exchange sums of the reduced rows
   float prim_f = 0.f, dual_f = 0.f;

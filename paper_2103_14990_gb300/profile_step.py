@@ -54,8 +54,10 @@ def main(argv=None) -> int:
         print(f"kernel {ms:.4f} ms  {1e3 * ms / a.iters:.2f} us/iteration  status {st[0]['status']}")
     if a.trace:
         tr = s.trace().astype(np.int64)
-        names = ["phi", "pre", "pass1", "pass2+final", "rest", "cta_sync", "barrier"]
-        pts = [(0, 1), (1, 6), (6, 7), (7, 2), (2, 3), (3, 4), (4, 5)]
+        # stamps: 0 top, 1 Phi-step, 7 pass 1 (+ y), 6 pass 2, 2 first patch done,
+        # 3 all patches, 4 CTA synchronised, 5 grid barrier passed
+        names = ["phi", "pass1", "pass2", "final", "rest", "cta_sync", "barrier"]
+        pts = [(0, 1), (1, 7), (7, 6), (6, 2), (2, 3), (3, 4), (4, 5)]
         for it in range(1, tr.shape[1] - 1):
             ok = tr[:, it, 0] > 0
             row = [np.median((tr[ok, it, b] - tr[ok, it, a_]) / 1e3) for a_, b in pts]
