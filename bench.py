@@ -46,6 +46,14 @@ def workload(name: str):
     return {"chain1024": I.chain1024, "chain10": I.chain10, "grid64": I.grid64}[name]()
 
 
+def bench_config(prob, world: int) -> dict:
+    """The workload description shared by both arms."""
+    return {"workload": prob.name, "n_sub": prob.n_sub, "T": prob.T, "d": prob.d, "boxes": "|x|<=1, |u|<=2",
+            "warm_start": "previous MPC step's Psi/Lambda (step 0 cold)", "max_iter": prob.max_iter,
+            "eps": prob.eps_p, "l2": "flushed between steps (256 MiB write outside the events)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def kernel_sha() -> str:
     return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
 
@@ -248,10 +256,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_dev / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded chain plant, x0 ~ U[-0.9,0.9])",
-        "config": {"workload": prob.name, "n_sub": n, "T": prob.T, "d": prob.d, "boxes": "|x|<=1, |u|<=2",
-                   "warm_start": "previous MPC step's Psi/Lambda (step 0 cold)", "max_iter": prob.max_iter,
-                   "eps": prob.eps_p, "l2": "flushed between steps (256 MiB write outside the events)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": bench_config(prob, world),
         "admm_iters_per_s": round(tot_iters / kern_s, 1),
         "iters_per_step": round(tot_iters / args.steps, 2),
         "steps_at_max_iter": int(sum(1 for s in status if s != 0)),
@@ -382,7 +387,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded chain plant, x0 ~ U[-0.9,0.9])", "impl": "reference",
-        "config": {"workload": prob.name, "n_sub": prob.n_sub, "T": prob.T, "d": prob.d},
+        "config": bench_config(prob, int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

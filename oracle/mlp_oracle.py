@@ -4,8 +4,11 @@ Three layers, x -> GELU(x W1 + b1) -> GELU(. W2 + b2) -> . W3 + b3, exact GELU
 0.5 x (1 + erf(x / sqrt 2)), loss = mean squared error.  Gradients by the
 chain rule, written out layer by layer.  `bf16=True` rounds the operands of
 every product to bfloat16 (round to nearest even) at the points where the GPU
-kernels hold them in BF16, with the products themselves in FP64.
-Pinned by finite differences in tests/test_mlp_oracle.py.
+kernels hold them in BF16, with the products themselves in FP64.  The
+optimiser is AdamW (Adam with bias-corrected moments and decoupled weight
+decay, Loshchilov & Hutter): w <- w (1 - lr wd) - lr m_hat / (sqrt(v_hat) + eps).
+Pinned by finite differences and closed-form Adam steps in
+tests/test_mlp_oracle.py.
 """
 import math
 
@@ -60,3 +63,15 @@ def loss_and_grads(P, x, t, bf16=False):
     G["W1"] = r(x).T @ r(dh1)
     G["b1"] = dh1.sum(0)
     return loss, G
+
+
+def adamw_step(w, g, m, v, step, lr, wd, b1=0.9, b2=0.999, eps=1e-8):
+    """One AdamW update of the flat parameter vector w (FP64) with gradient g
+    and moment estimates m, v after `step - 1` updates; returns (w, m, v)."""
+    w, g, m, v = (np.asarray(a, np.float64) for a in (w, g, m, v))
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    m_hat = m / (1.0 - b1 ** step)
+    v_hat = v / (1.0 - b2 ** step)
+    w = w * (1.0 - lr * wd) - lr * m_hat / (np.sqrt(v_hat) + eps)
+    return w, m, v

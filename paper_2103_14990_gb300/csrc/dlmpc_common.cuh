@@ -23,23 +23,6 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
   return v;
 }
 
-// Relaxed (strong, no ordering) loads for polling: unlike an acquire load
-// they leave the SM's L1 contents alone.  A poll that sees the value it waits
-// for is followed by one fence (acquire pattern), see fence_acquire.
-__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-
 __device__ __forceinline__ int ld_volatile_i32(const int32_t *p) {
   return *reinterpret_cast<const volatile int32_t *>(p);
 }

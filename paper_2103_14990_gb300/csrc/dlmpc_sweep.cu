@@ -716,11 +716,8 @@ __device__ __forceinline__ bool sweep_barrier(const Params &P, unsigned e, unsig
     int ok = 1;
     unsigned long long v = 0;
     for (unsigned spins = 0;; ++spins) {
-      v = ld_relaxed_u64(ctr);
-      if ((unsigned)(v & 0xffffffffull) >= target) {
-        fence_acquire();
-        break;
-      }
+      v = ld_acquire_u64(ctr);  // (measured: cheaper than relaxed polls plus one fence)
+      if ((unsigned)(v & 0xffffffffull) >= target) break;
       if ((spins & 63u) == 63u) {
         if (ld_volatile_i32(P.err) != 0) { ok = 0; break; }
         if (global_ns() - t0 > P.timeout_ns) {

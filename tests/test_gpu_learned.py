@@ -54,6 +54,28 @@ def test_gradients_match_oracle(small_net):
         assert relerr(G[name], G_64[name]) < 3e-2, name       # BF16 against exact
 
 
+def test_adamw_steps_match_oracle():
+    """Three training steps: each GPU update against the oracle's AdamW applied
+    to the GPU's own gradient of that step (isolates the optimiser kernel)."""
+    import torch
+    import paper_2103_14990_gb300 as pkg
+    rng = np.random.default_rng(4)
+    mlp = pkg.MLP(10, 64, 12, seed=7)
+    x = torch.tensor(rng.uniform(-1, 1, (96, 10)), dtype=torch.float32, device="cuda")
+    t = torch.tensor(rng.normal(size=(96, 12)), dtype=torch.float32, device="cuda")
+    w = mlp.get_params().astype(np.float64)
+    m = np.zeros_like(w)
+    v = np.zeros_like(w)
+    lr, wd = 2e-3, 0.05
+    for step in range(1, 4):
+        g, _ = mlp.gradients(x, t)
+        mlp.train_step(x, t, lr, wd)
+        w_ref, m, v = M.adamw_step(w, g.astype(np.float64), m, v, step, lr, wd)
+        w_gpu = mlp.get_params().astype(np.float64)
+        assert relerr(w_gpu - w, w_ref - w) < 1e-4, step
+        w = w_gpu
+
+
 def test_training_reduces_loss():
     import torch
     import paper_2103_14990_gb300 as pkg

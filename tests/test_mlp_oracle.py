@@ -1,5 +1,6 @@
 """Pins of the FP64 warm-start network oracle: finite differences of every
-parameter gradient on a small network, the GELU derivative, bf16 rounding."""
+parameter gradient on a small network, the GELU derivative, bf16 rounding,
+closed-form AdamW steps."""
 import numpy as np
 
 from oracle import mlp_oracle as M
@@ -45,3 +46,27 @@ def test_bf16_rounding():
     assert M.round_bf16(np.array([1.0 + 3 * 2 ** -8]))[0] == 1.0 + 2 ** -6
     v = np.random.default_rng(1).normal(size=1000)
     assert np.max(np.abs(M.round_bf16(v) - v) / np.abs(v)) <= 2 ** -8
+
+
+def test_adamw_first_step_is_a_sign_step():
+    # from m = v = 0 the bias-corrected moments are g and g^2 exactly:
+    # w1 = w0 (1 - lr wd) - lr g / (|g| + eps)
+    rng = np.random.default_rng(2)
+    w0, g = rng.normal(size=50), rng.normal(size=50)
+    lr, wd, eps = 1e-2, 0.1, 1e-8
+    w1, m, v = M.adamw_step(w0, g, np.zeros(50), np.zeros(50), 1, lr, wd, eps=eps)
+    assert np.allclose(w1, w0 * (1 - lr * wd) - lr * g / (np.abs(g) + eps), rtol=0, atol=1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_adamw_constant_gradient_moves_by_lr_each_step():
+    # with a constant gradient the bias corrections make m_hat = g and
+    # v_hat = g^2 at every step, so each step (no decay) moves by lr g / (|g| + eps)
+    rng = np.random.default_rng(3)
+    w, g = rng.normal(size=20), rng.normal(size=20)
+    m, v = np.zeros(20), np.zeros(20)
+    lr = 3e-3
+    for step in range(1, 30):
+        w_new, m, v = M.adamw_step(w, g, m, v, step, lr, 0.0)
+        assert np.allclose(w - w_new, lr * g / (np.abs(g) + 1e-8), rtol=1e-9, atol=0)
+        w = w_new
