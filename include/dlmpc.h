@@ -109,7 +109,8 @@ typedef struct {
 #define DLMPC_OPT_MAX_ITER 2      /* overrides every instance's max_iter */
 #define DLMPC_OPT_TIMEOUT_MS 3    /* bound of every device-side wait (default 2000) */
 #define DLMPC_OPT_EXPORT_PHI 4    /* != 0: keep the last Phi for dlmpc_get_state */
-#define DLMPC_OPT_SWEEP_SHAPE 5   /* sweep launch: threads per group * 10000 + groups per CTA * 100
+#define DLMPC_OPT_SWEEP_SHAPE 5   /* sweep launch: threads per group (64, 96, 128 or 256) * 10000
+                                     + groups per CTA (1..15, at most 1024 threads) * 100
                                      + Phi-step wave (e.g. 1280402); replans the launch */
 #define DLMPC_OPT_TIMING 7        /* != 0: record CUDA events around every step (dlmpc_get_timing) */
 #define DLMPC_OPT_TRACE 9         /* != 0: record phase timestamps of the sweep (dlmpc_get_trace) */

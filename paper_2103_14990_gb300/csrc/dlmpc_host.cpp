@@ -607,7 +607,7 @@ std::vector<std::vector<int32_t>> lpt(const dlmpc_ctx *ctx, const std::vector<in
 // filled with resident Psi/Lambda and q, then resident N, until it is full.
 int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = false) {
   // named barrier ids 1..15 serve the groups (id 0 is __syncthreads)
-  if (!(gt == 64 || gt == 128 || gt == 256) || ng < 1 || ng > 15 || gt * ng > 1024 || wave < 1 || wave > 8)
+  if (!(gt == 64 || gt == 96 || gt == 128 || gt == 256) || ng < 1 || ng > 15 || gt * ng > 1024 || wave < 1 || wave > 8)
     return ctx->fail(DLMPC_ERR_ARG, "unsupported sweep shape");
   if (ctx->max_kpad > 4 * gt) return ctx->fail(DLMPC_ERR_ARG, "null-space dimension too large for this group size");
   const int nx = ctx->nx;
@@ -1175,7 +1175,7 @@ extern "C" int dlmpc_autotune(dlmpc_ctx *ctx, const float *x_dev, int32_t iters,
   ctx->trace = 0;
   std::vector<dlmpc_tune_entry> tried;
   dlmpc_tune_entry best{0, 0, 0, 0, std::numeric_limits<float>::infinity()};
-  static const int kGt[] = {64, 128, 256};
+  static const int kGt[] = {64, 96, 128, 256};
   static const int kNg[] = {1, 2, 4, 6, 8, 12, 15};
   static const int kWave[] = {1, 2};
   static const int kRes[] = {2, 1};

@@ -318,10 +318,11 @@ __device__ __forceinline__ void finish_item(const Params &P, int idx, const Item
   group_sync(g, GT);
   if (gt < 32) {
     // lane w < kWarps holds warp w's sums; FP64 tree over the lanes
+    constexpr int kTree = kWarps <= 1 ? 1 : kWarps <= 2 ? 2 : kWarps <= 4 ? 4 : 8;  // power of two >= kWarps
     double pp = gt < kWarps ? G.red[2 * gt] : 0.0;
     double dd = gt < kWarps ? G.red[2 * gt + 1] : 0.0;
 #pragma unroll
-    for (int o = kWarps / 2; o > 0; o >>= 1) {
+    for (int o = kTree / 2; o > 0; o >>= 1) {
       pp += __shfl_xor_sync(0xffffffffu, pp, o);
       dd += __shfl_xor_sync(0xffffffffu, dd, o);
     }
@@ -500,17 +501,22 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
 // Both passes read their matrix flat: thread (q, g) owns the 16-byte column
 // group g of every QS-th row starting at row q, so a warp reads consecutive
 // 16-byte units, and the QS partial sums per output are added afterwards.
+// floor(a / b) for 0 <= a < 2^16, 1 <= b < 2^12: the quotient of a + 1/2 is
+// at least 1/(2b) away from an integer, far beyond the few-ulp error of the
+// fast division, so the float result floors exactly (no integer division).
+__device__ __forceinline__ int small_div(int a, int b) { return (int)__fdividef((float)a + 0.5f, (float)b); }
+
 template <int U>
 __device__ __forceinline__ void flat_pass(const float *M, int rows, int ld, const float *vec, float *part, int gt,
                                           int GT) {
   const int ng4 = ld >> 2;
-  const int QS = GT >= ng4 ? GT / ng4 : 1;
+  const int QS = GT >= ng4 ? small_div(GT, ng4) : 1;
   for (int e = gt; e < QS * ng4; e += GT) {  // one round unless ld > 4 GT
-    const int q = e / ng4, cg = e - q * ng4;
+    const int q = small_div(e, ng4), cg = e - q * ng4;
     const float *mp = M + q * ld + 4 * cg;
     const float *vp = vec + q;
     const int step = QS * ld;
-    int left = rows > q ? (rows - q + QS - 1) / QS : 0;  // rows of this thread
+    int left = rows > q ? small_div(rows - q + QS - 1, QS) : 0;  // rows of this thread
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     // whole chunks of U rows without predicates (running pointers), then
     // one predicated tail chunk
@@ -582,7 +588,7 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
   group_sync(g, GT);
   {
     const int ncg = kpad >> 2;
-    const int QS = GT >= ncg ? GT / ncg : 1;
+    const int QS = GT >= ncg ? small_div(GT, ncg) : 1;
     for (int a = gt; a < kpad; a += GT) {
       float y = 0.f;
       if (a < k)
@@ -603,7 +609,7 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
   float prim_f = 0.f, dual_f = 0.f;
   {
     const int nrg = dpad >> 2;
-    const int QS = GT >= nrg ? GT / nrg : 1;
+    const int QS = GT >= nrg ? small_div(GT, nrg) : 1;
     for (int red = gt; red < dred; red += GT) {
       float o = 0.f;
       for (int q = 0; q < QS; ++q) o += G.part[q * dpad + red];
@@ -970,6 +976,7 @@ const void *sweep_kernel_ptr(int nx, int gt) {
 #define DLMPC_SWEEP_CASE(NXV)                    \
   case NXV:                                      \
     if (gt == 64) return sweep_fn<NXV, 64>();    \
+    if (gt == 96) return sweep_fn<NXV, 96>();    \
     if (gt == 128) return sweep_fn<NXV, 128>();  \
     if (gt == 256) return sweep_fn<NXV, 256>();  \
     return nullptr;
