@@ -78,3 +78,79 @@ def test_batch_sampled_operators():
             assert np.max(np.abs(q - blk.q)) < 5e-6, p.name
         off += p.n_sub
     s.close()
+
+
+def _one_iteration_check(s, probs, samples, torch, K=9):
+    """K iterations from x(0), then one more from the state left behind, in
+    the launch configuration the autotuner picks.  The last iteration is
+    checked against the oracle's steps: the Phi-step on every row, the
+    Psi-step on sampled column patches (projection of the GPU's own Phi +
+    Lambda_prev), the Lambda-step everywhere."""
+    import paper_2103_14990_gb300 as pkg
+    x = torch.tensor(np.concatenate([p.x0 for p in probs]).astype(np.float32), device="cuda")
+    u = torch.zeros(x.shape[0], probs[0].nu, device="cuda")
+    s.autotune(x, iters=4)
+    s.set_option(pkg.OPT_EXPORT_PHI, 1)
+    s.set_option(pkg.OPT_FIXED_ITERS, K)
+    s.step(x, u, None, warm=pkg.WARM_COLD)
+    _, psi0, lam0 = (a.cpu().numpy().astype(np.float64) if a is not None else None for a in s.get_state())
+    s.set_option(pkg.OPT_FIXED_ITERS, 1)
+    s.step(x, u, None, warm=pkg.WARM_PREVIOUS)
+    phi1, psi1, lam1 = (a.cpu().numpy().astype(np.float64) for a in s.get_state(phi=True))
+    off = 0
+    for b, p in enumerate(probs):
+        lay = O.Layout(p)
+        sl = slice(off, off + lay.nnz)
+        ref_phi, _ = O.phi_step(lay, psi0[sl], lam0[sl], p.x0, p.rho)
+        assert rel(phi1[sl], ref_phi) <= 1e-4, p.name
+        assert rel(lam1[sl], lam0[sl] + phi1[sl] - psi1[sl]) <= 1e-5, p.name
+        for j in samples(b, p):
+            blk = O.column_block(p, j)
+            for a in range(p.nx):
+                c = slice(off + lay.col_off[j * p.nx + a], off + lay.col_off[j * p.nx + a + 1])
+                v = phi1[c] + lam0[c]
+                assert rel(psi1[c], blk.P @ v + blk.q[a]) <= 1e-4, (p.name, j, a)
+        off += lay.nnz
+    assert off == phi1.size
+
+
+def _compact_matches_full(s, probs, torch, K=20):
+    """K iterations on the compact iterate against K in the full form."""
+    import paper_2103_14990_gb300 as pkg
+    x = torch.tensor(np.concatenate([p.x0 for p in probs]).astype(np.float32), device="cuda")
+    u = torch.zeros(sum(p.n_sub for p in probs), probs[0].nu, device="cuda")
+    out = []
+    for compact in (1, 0):
+        s.set_option(pkg.OPT_EXPORT_PHI, 0)
+        s.set_option(pkg.OPT_COMPACT, compact)
+        s.set_option(pkg.OPT_FIXED_ITERS, K)
+        s.step(x, u, None, warm=pkg.WARM_COLD)
+        _, psi, lam = s.get_state()
+        out.append((psi.cpu().numpy(), lam.cpu().numpy(), u.cpu().numpy().copy()))
+    s.set_option(pkg.OPT_COMPACT, 1)
+    for a, b in zip(out[0], out[1]):
+        assert rel(a, b) <= 1e-4
+
+
+def test_grid64_sampled_iteration():
+    import torch
+    import paper_2103_14990_gb300 as pkg
+    p = I.grid64()
+    s = pkg.Solver([p])
+    corners_edges = [0, 63, 4032, 4095, 1, 64, 2 * 64 + 2, 30 * 64 + 31, 64 * 10 + 63, 4094]
+    _one_iteration_check(s, [p], lambda b, q: corners_edges, torch)
+    _compact_matches_full(s, [p], torch)
+    s.close()
+
+
+def test_batch256_sampled_iteration():
+    import torch
+    import paper_2103_14990_gb300 as pkg
+    probs = I.batch256()
+    s = pkg.Solver(probs)
+    picked = [0, 1, 17, 128, 255]
+    # the Phi- and Lambda-steps of every instance, the Psi-step of a few
+    # patches (ends, middle) of a few instances
+    _one_iteration_check(s, probs, lambda b, q: ([0, q.n_sub // 2, q.n_sub - 1] if b in picked else []), torch)
+    _compact_matches_full(s, probs, torch)
+    s.close()
