@@ -10,6 +10,9 @@ null-space basis instead).
 
 Pinned parts (see tests/test_oracle_pins.py):
   * phi_step      - brute-force / KKT checks of the row box-QP and its special cases;
+  * box_qp, phi_step_block (full Q_i, R_i blocks) - against scipy's bounded
+                    minimiser, the diagonal closed form, the Riccati gain with
+                    full blocks and the centralised boxed QP with full blocks;
   * psi projector - Z psi = e exactly, idempotent symmetric projector, min-norm offset
                     against lstsq, residual orthogonal to the null space;
   * admm / mpc    - converged trajectory against the centralised
@@ -39,6 +42,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import itertools
 from typing import Dict, List, Optional
 
 import numpy as np
@@ -283,6 +287,69 @@ def phi_step(lay: Layout, Psi: np.ndarray, Lam: np.ndarray, x0: np.ndarray, rho:
     return Phi, z
 
 
+def box_qp(H: np.ndarray, c: np.ndarray, lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
+    """argmin 1/2 z^T H z - c^T z  s.t. lo <= z <= hi, H symmetric positive
+    definite, n <= 4.  Active-set enumeration: every component is free, at lo
+    or at hi (only finite bounds); the free part solves H_FF z_F = c_F - H_FA z_A,
+    and the pattern is accepted when z is feasible and the gradient
+    g = H z - c satisfies the KKT signs (g >= 0 at lo, g <= 0 at hi).  The
+    optimum of a strictly convex QP is unique, so exactly one pattern fits
+    (up to degenerate ties, which give the same z)."""
+    n = len(c)
+    choices = [[0] + ([1] if np.isfinite(lo[a]) else []) + ([2] if np.isfinite(hi[a]) else []) for a in range(n)]
+    tol = 1e-12 * (1.0 + np.max(np.abs(c)) + np.max(np.abs(H)))
+    for pattern in itertools.product(*choices):
+        z = np.zeros(n)
+        free = [a for a in range(n) if pattern[a] == 0]
+        fixed = [a for a in range(n) if pattern[a] != 0]
+        for a in fixed:
+            z[a] = lo[a] if pattern[a] == 1 else hi[a]
+        if free:
+            rhs = c[free] - H[np.ix_(free, fixed)] @ z[fixed] if fixed else c[free]
+            z[free] = np.linalg.solve(H[np.ix_(free, free)], rhs)
+        if np.any(z < lo - tol) or np.any(z > hi + tol):
+            continue
+        g = H @ z - c
+        if all((pattern[a] == 1 and g[a] >= -tol) or (pattern[a] == 2 and g[a] <= tol) for a in fixed):
+            return z
+    raise RuntimeError("box_qp: no KKT point (H not positive definite?)")
+
+
+def phi_step_block(lay: Layout, Psi: np.ndarray, Lam: np.ndarray, x0: np.ndarray, rho: float):
+    """Phi-comp with full cost blocks Q_i, R_i (Sec. II-A with non-diagonal
+    Q_t, R_t): the rows of subsystem i at one time slot (its nx state rows, or
+    its nu input rows) share x_hat_i, so with w = (Psi - Lambda) x_hat per row,
+    s = ||x_hat_i||^2 and z = Phi x_hat, the slot's rows solve
+        min z^T Q_i z + rho/(2 s) ||z - w||^2  s.t.  lo <= z <= hi,
+    a box-QP with H = 2 Q_i + (rho/s) I and c = (rho/s) w (box_qp); each row is
+    then v + ((z - w)/s) x_hat.  s = 0 gives phi = v.  Returns (Phi, z)."""
+    prob = lay.prob
+    nx, nu, T = prob.nx, prob.nu, prob.T
+    xf = x0.reshape(-1)
+    xe = xf[lay.cols]
+    V = Psi - Lam
+    w = np.bincount(lay.rows, weights=V * xe, minlength=lay.n_rows)
+    s = np.bincount(lay.rows, weights=xe * xe, minlength=lay.n_rows)
+    Qb = prob.Q_blk if prob.Q_blk is not None else np.array([np.diag(q) for q in prob.q])
+    Rb = prob.R_blk if prob.R_blk is not None else np.array([np.diag(r) for r in prob.r])
+    z = w.copy()
+    alpha = np.zeros(lay.n_rows)
+    for i in range(prob.n_sub):
+        groups = [([global_row(prob, i, t * nx + a) for a in range(nx)], Qb[i]) for t in range(T)]
+        groups += [([global_row(prob, i, nx * T + t * nu + b) for b in range(nu)], Rb[i]) for t in range(T - 1)]
+        for rows, C in groups:
+            rows = np.asarray(rows)
+            si = s[rows[0]]
+            if si == 0.0:
+                continue
+            H = 2.0 * C + (rho / si) * np.eye(len(rows))
+            zz = box_qp(H, (rho / si) * w[rows], lay.lo[rows], lay.hi[rows])
+            z[rows] = zz
+            alpha[rows] = (zz - w[rows]) / si
+    Phi = V + alpha[lay.rows] * xe
+    return Phi, z
+
+
 def psi_step(lay: Layout, blocks: List[ColumnBlock], V: np.ndarray) -> np.ndarray:
     """Column-wise Psi-comp: psi_c = argmin ||psi - v_c|| s.t. Z_j psi = e_c,
     i.e. psi = P_j v + Z_j^+ e_c, for every column c of every subsystem j."""
@@ -341,8 +408,9 @@ def admm(lay: Layout, blocks: List[ColumnBlock], x0: np.ndarray, *,
     it = 0
     r_max = s_max = np.inf
     Phi = z = None
+    block = prob.Q_blk is not None or prob.R_blk is not None
     for it in range(1, n_it + 1):
-        Phi, z = phi_step(lay, Psi, Lam, x0, rho)
+        Phi, z = (phi_step_block if block else phi_step)(lay, Psi, Lam, x0, rho)
         Psi_new = psi_step(lay, blocks, Phi + Lam)
         Lam = Lam + Phi - Psi_new
         r_max = float(np.max(per_subsystem_norm(lay, Phi - Psi_new)))

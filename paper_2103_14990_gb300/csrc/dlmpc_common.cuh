@@ -101,4 +101,69 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsign
   }
 }
 
+// ---------------------------------------------------------------------------
+// flat matrix-vector pass (sweep and learned start)
+// ---------------------------------------------------------------------------
+// part[q][4g..4g+3] = sum over rows r = q, q + QS, ... of M[r][4g..4g+3] vec[r]
+// for a row-major M (ld floats per row, 16-byte aligned rows): thread (q, g)
+// owns one 16-byte column group and every QS-th row (QS = GT / (ld / 4)), so a
+// warp reads consecutive 16-byte units; the caller adds the QS partials.
+
+// floor(a / b) for 0 <= a < 2^16, 1 <= b < 2^12: the quotient of a + 1/2 is
+// at least 1/(2b) away from an integer, far beyond the few-ulp error of the
+// fast division, so the float result floors exactly (no integer division).
+__device__ __forceinline__ int small_div(int a, int b) { return (int)__fdividef((float)a + 0.5f, (float)b); }
+
+template <int U>
+__device__ __forceinline__ void flat_pass(const float *M, int rows, int ld, const float *vec, float *part, int gt,
+                                          int GT) {
+  const int ng4 = ld >> 2;
+  const int QS = GT >= ng4 ? small_div(GT, ng4) : 1;
+  for (int e = gt; e < QS * ng4; e += GT) {  // one round unless ld > 4 GT
+    const int q = small_div(e, ng4), cg = e - q * ng4;
+    const float *mp = M + q * ld + 4 * cg;
+    const float *vp = vec + q;
+    const int step = QS * ld;
+    int left = rows > q ? small_div(rows - q + QS - 1, QS) : 0;  // rows of this thread
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    // whole chunks of U rows without predicates (running pointers), then
+    // one predicated tail chunk
+    for (; left >= U; left -= U) {
+      float4 m4[U];
+      float vv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        m4[u] = *reinterpret_cast<const float4 *>(mp + u * step);
+        vv[u] = vp[u * QS];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        acc.x = fmaf(m4[u].x, vv[u], acc.x);
+        acc.y = fmaf(m4[u].y, vv[u], acc.y);
+        acc.z = fmaf(m4[u].z, vv[u], acc.z);
+        acc.w = fmaf(m4[u].w, vv[u], acc.w);
+      }
+      mp += U * step;
+      vp += U * QS;
+    }
+    if (left > 0) {
+      float4 m4[U];
+      float vv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        m4[u] = u < left ? *reinterpret_cast<const float4 *>(mp + u * step) : make_float4(0.f, 0.f, 0.f, 0.f);
+        vv[u] = u < left ? vp[u * QS] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        acc.x = fmaf(m4[u].x, vv[u], acc.x);
+        acc.y = fmaf(m4[u].y, vv[u], acc.y);
+        acc.z = fmaf(m4[u].z, vv[u], acc.z);
+        acc.w = fmaf(m4[u].w, vv[u], acc.w);
+      }
+    }
+    *reinterpret_cast<float4 *>(part + q * ld + 4 * cg) = acc;
+  }
+}
+
 }  // namespace dlmpc

@@ -26,6 +26,7 @@ cudaError_t launch_repack(const Item *scratch_items, const Item *items, int n_it
                           cudaStream_t s);
 const void *sweep_kernel_ptr(int nx, int gt);
 int sweep_group_floats(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad, int max_kpad, int max_nmem);
+cudaStream_t mlp_stream(const dlmpc_mlp *mlp);
 cudaError_t launch_sweep(const Params &P, int gt, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_stats(const int32_t *inst_item_ptr, int n_inst, const float *item_r, const float *item_s,
                          const int32_t *inst_iters, const int32_t *err, int fixed, const float *epsp,
@@ -189,11 +190,14 @@ struct dlmpc_ctx {
   DevBuf<int32_t> d_row_sub, d_row_loc;
   float *h_exchange = nullptr;  // pinned, state_floats
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_learn[2] = {nullptr, nullptr};
 
   ~dlmpc_ctx() {
     if (h_stats) cudaFreeHost(h_stats);
     if (h_err) cudaFreeHost(h_err);
     for (auto &e : ev)
+      if (e) cudaEventDestroy(e);
+    for (auto &e : ev_learn)
       if (e) cudaEventDestroy(e);
     for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
     if (capture_stream) cudaStreamDestroy(capture_stream);
@@ -886,8 +890,21 @@ int learned_start(dlmpc_ctx *ctx, const float *x_dev) {
   cudaStream_t s = ctx->stream;
   const LearnArgs A = learn_args(ctx);
   CK(launch_learn_features(A, x_dev, ctx->d_feat.p, s), "learn_features");
+  // the network may run on another stream: order it between the features and
+  // the scatter of its output
+  const cudaStream_t ms = mlp_stream(ctx->mlp);
+  if (ms != s) {
+    for (auto &e : ctx->ev_learn)
+      if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+    CK(cudaEventRecord(ctx->ev_learn[0], s), "event");
+    CK(cudaStreamWaitEvent(ms, ctx->ev_learn[0], 0), "stream wait");
+  }
   const int rc = dlmpc_mlp_forward(ctx->mlp, ctx->d_feat.p, ctx->n_sub, ctx->d_lout.p);
   if (rc) return ctx->fail(rc, std::string("network forward: ") + dlmpc_mlp_last_error(ctx->mlp));
+  if (ms != s) {
+    CK(cudaEventRecord(ctx->ev_learn[1], ms), "event");
+    CK(cudaStreamWaitEvent(s, ctx->ev_learn[1], 0), "stream wait");
+  }
   CK(launch_learn_rows(A, ctx->d_phi_l.p, ctx->d_lam.p, ctx->d_lout.p, 1, s), "learn_rows");
   CK(launch_learn_init(ctx->d_items.p, ctx->n_sub, ctx->nx, ctx->max_dred_pad, ctx->max_kpad, ctx->d_N.p, ctx->d_q.p,
                        ctx->d_phi_l.p, ctx->d_psi.p, ctx->d_lam.p, s),

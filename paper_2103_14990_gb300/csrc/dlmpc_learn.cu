@@ -9,8 +9,11 @@
 // column c of j at item j, column c, position of i in Patch(j), row r.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cstdint>
 
+#include "dlmpc_common.cuh"
 #include "dlmpc_internal.h"
 
 namespace dlmpc {
@@ -89,46 +92,72 @@ __global__ void learn_rows_kernel(LearnArgs A, float *phi, float *lam, float *ro
 }
 
 // Psi0 = proj(v) with v = Phi~ + Lambda~ (Psi-comp), Lambda0 = v - Psi0.
-// One CTA per patch; N and q from global memory.  In: phi, lam hold Phi~,
-// Lambda~; out: psi, lam hold Psi0, Lambda0.
-__global__ void learn_init_kernel(const Item *items, int n_items, int nx, const float *Nmat, const float *qvec,
-                                  const float *phi, float *psi, float *lam) {
-  extern __shared__ float smv[];  // [nx][dred] v, then [nx][kpad] t
+// One CTA of kInitThreads per patch; per own column c: t = N^T v_c (flat pass
+// over N), psi = q_c + N t (flat pass over N^T, stored after N), both read
+// from global memory.  In: phi, lam hold Phi~, Lambda~; out: psi, lam hold
+// Psi0, Lambda0.
+constexpr int kInitThreads = 128;
+
+__global__ void __launch_bounds__(kInitThreads) learn_init_kernel(const Item *items, int n_items, int nx,
+                                                                  const float *Nmat, const float *qvec,
+                                                                  const float *phi, float *psi, float *lam,
+                                                                  int part_floats) {
+  extern __shared__ __align__(16) float smv[];  // v [dred_pad], t [kpad], part [part_floats]
   const int j = blockIdx.x;
   if (j >= n_items) return;
   const Item it = items[j];
+  const int gt = threadIdx.x;
   const int dcol = it.r_sub * it.n_mem, rs_red = it.r_sub - nx;
   float *v = smv;
-  float *t = smv + nx * it.dred;
+  float *t = smv + it.dred_pad;
+  float *part = t + it.kpad;
   const float *N = Nmat + it.n_off;
-  for (int e = threadIdx.x; e < nx * dcol; e += blockDim.x) {
-    const int c = e / dcol, f = e % dcol;
-    const int mpos = f / it.r_sub, r = f % it.r_sub;
-    if (r >= nx) v[c * it.dred + mpos * rs_red + r - nx] = phi[it.st_off + e] + lam[it.st_off + e];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < nx * it.k; e += blockDim.x) {
-    const int c = e / it.k, a = e % it.k;
-    float s = 0.f;
-    for (int red = 0; red < it.dred; ++red) s += N[(int64_t)red * it.kpad + a] * v[c * it.dred + red];
-    t[c * it.kpad + a] = s;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < nx * dcol; e += blockDim.x) {
-    const int c = e / dcol, f = e % dcol;
-    const int mpos = f / it.r_sub, r = f % it.r_sub;
-    const float vv = phi[it.st_off + e] + lam[it.st_off + e];
-    float ps;
-    if (r < nx) {
-      ps = (mpos == it.self_pos && r == c) ? 1.f : 0.f;
-    } else {
-      const int red = mpos * rs_red + r - nx;
-      float s = qvec[it.q_off + (int64_t)c * it.dred_pad + red];
-      for (int a = 0; a < it.k; ++a) s += N[(int64_t)red * it.kpad + a] * t[c * it.kpad + a];
-      ps = s;
+  const float *NT = N + (int64_t)it.dred_pad * it.kpad;
+  for (int c = 0; c < nx; ++c) {
+    const int64_t col = it.st_off + (int64_t)c * dcol;
+    for (int red = gt; red < it.dred_pad; red += kInitThreads) {
+      float vv = 0.f;
+      if (red < it.dred) {
+        const int mpos = small_div(red, rs_red);
+        const int f = red + (mpos + 1) * nx;
+        vv = phi[col + f] + lam[col + f];
+      }
+      v[red] = vv;
     }
-    psi[it.st_off + e] = ps;
-    lam[it.st_off + e] = vv - ps;
+    __syncthreads();
+    flat_pass<8>(N, it.dred, it.kpad, v, part, gt, kInitThreads);
+    __syncthreads();
+    {
+      const int ncg = it.kpad >> 2;
+      const int QS = kInitThreads >= ncg ? small_div(kInitThreads, ncg) : 1;
+      for (int a = gt; a < it.kpad; a += kInitThreads) {
+        float s = 0.f;
+        if (a < it.k)
+          for (int q = 0; q < QS; ++q) s += part[q * it.kpad + a];
+        t[a] = s;
+      }
+    }
+    __syncthreads();
+    flat_pass<8>(NT, it.k, it.dred_pad, t, part, gt, kInitThreads);
+    __syncthreads();
+    const int nrg = it.dred_pad >> 2;
+    const int QS = kInitThreads >= nrg ? small_div(kInitThreads, nrg) : 1;
+    for (int f = gt; f < dcol; f += kInitThreads) {
+      const int mpos = small_div(f, it.r_sub), r = f - mpos * it.r_sub;
+      const float vv = phi[col + f] + lam[col + f];
+      float ps;
+      if (r < nx) {
+        ps = (mpos == it.self_pos && r == c) ? 1.f : 0.f;
+      } else {
+        const int red = mpos * rs_red + r - nx;
+        float s = qvec[it.q_off + (int64_t)c * it.dred_pad + red];
+        for (int q = 0; q < QS; ++q) s += part[q * it.dred_pad + red];
+        ps = s;
+      }
+      psi[col + f] = ps;
+      lam[col + f] = vv - ps;
+    }
+    __syncthreads();
   }
 }
 
@@ -144,12 +173,14 @@ cudaError_t launch_learn_rows(const LearnArgs &A, float *phi, float *lam, float 
 
 cudaError_t launch_learn_init(const Item *items, int n_items, int nx, int max_dred, int max_kpad, const float *Nmat,
                               const float *qvec, const float *phi, float *psi, float *lam, cudaStream_t s) {
-  const size_t smem = (size_t)nx * (max_dred + max_kpad) * 4;
+  // partial sums of a flat pass: at most 4 * threads, or one row when it is wider
+  const int part = std::max(std::max(4 * kInitThreads, max_dred), max_kpad);
+  const size_t smem = (size_t)(max_dred + max_kpad + part) * 4;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(learn_init_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  learn_init_kernel<<<n_items, 256, smem, s>>>(items, n_items, nx, Nmat, qvec, phi, psi, lam);
+  learn_init_kernel<<<n_items, kInitThreads, smem, s>>>(items, n_items, nx, Nmat, qvec, phi, psi, lam, part);
   return cudaGetLastError();
 }
 

@@ -373,6 +373,12 @@ extern "C" int dlmpc_mlp_get_params(dlmpc_mlp *mlp, float *params, int64_t n) {
   return DLMPC_OK;
 }
 
+namespace dlmpc {
+// The stream the network's kernels run on (for callers that order it against
+// their own stream).
+cudaStream_t mlp_stream(const dlmpc_mlp *mlp) { return mlp->stream; }
+}  // namespace dlmpc
+
 extern "C" int dlmpc_mlp_forward(dlmpc_mlp *mlp, const float *x_dev, int32_t n, float *y_dev) {
   if (!mlp || !x_dev || !y_dev || n < 1) return DLMPC_ERR_ARG;
   return forward(mlp, x_dev, n, y_dev, true);

@@ -61,6 +61,8 @@ class Problem:
     name: str = ""
     graph: str = "chain"        # "chain" or "grid"
     grid_shape: Optional[tuple] = None
+    Q_blk: Optional[np.ndarray] = None  # f64 [n_sub, nx, nx] full SPD Q_i (replaces q), or None
+    R_blk: Optional[np.ndarray] = None  # f64 [n_sub, nu, nu] full SPD R_i (replaces r), or None
 
     @property
     def r_sub(self) -> int:
@@ -183,6 +185,26 @@ def make_instance(n: int, T: int, d: int, *, graph: str = "chain", seed: int = 0
                    x_lo=x_lo, x_hi=x_hi, u_lo=u_lo, u_hi=u_hi,
                    rho=rho, eps_p=eps, eps_d=eps, max_iter=max_iter, x0=x0,
                    mpc_steps=mpc_steps, name=name, graph=graph, grid_shape=shape)
+
+
+def with_block_costs(p: Problem, seed: int, coupling: float = 0.5) -> Problem:
+    """A copy of p whose cost blocks Q_i, R_i are full symmetric positive
+    definite matrices: M M^T / n + 0.5 I with M ~ U[-coupling, coupling] plus
+    the identity (numpy PCG64 `default_rng(seed)`, Q_i then R_i per subsystem,
+    subsystem-major).  The diagonal q, r are set to the blocks' diagonals."""
+    rng = np.random.default_rng(seed)
+    nx, nu = p.nx, p.nu
+    Q = np.empty((p.n_sub, nx, nx))
+    R = np.empty((p.n_sub, nu, nu))
+    for i in range(p.n_sub):
+        M = np.eye(nx) + rng.uniform(-coupling, coupling, (nx, nx))
+        Q[i] = M @ M.T / nx + 0.5 * np.eye(nx)
+        M = np.eye(nu) + rng.uniform(-coupling, coupling, (nu, nu))
+        R[i] = M @ M.T / nu + 0.5 * np.eye(nu)
+    out = dataclasses.replace(p, Q_blk=Q, R_blk=R, q=np.array([np.diag(b) for b in Q]),
+                              r=np.array([np.diag(b) for b in R]),
+                              name=(p.name + "_blockQR") if p.name else "")
+    return out
 
 
 # --- the five workloads -------------------------------------------------------

@@ -353,3 +353,149 @@ def test_dual_update_and_closed_loop_dynamics_consistency():
     x1 = y[Nx:2 * Nx]
     u0 = y[p.T * Nx:p.T * Nx + p.n_sub]
     assert np.allclose(x1, p.dense_A() @ p.x0.reshape(-1) + p.dense_B() @ u0, atol=1e-8)
+
+
+# --------------------------------------------------------------------------
+# Full cost blocks Q_i, R_i (box-QP Phi-step)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(8))
+def test_box_qp_matches_bounded_minimiser(seed):
+    rng = np.random.default_rng(seed)
+    n = 1 + seed % 4
+    M = rng.normal(size=(n, n))
+    H = M @ M.T + 0.2 * np.eye(n)
+    c = rng.normal(size=n) * 3
+    lo = np.where(rng.random(n) < 0.8, -rng.uniform(0.1, 1.0, n), -np.inf)
+    hi = np.where(rng.random(n) < 0.8, rng.uniform(0.1, 1.0, n), np.inf)
+    z = O.box_qp(H, c, lo, hi)
+    ref = scipy.optimize.minimize(lambda v: 0.5 * v @ H @ v - c @ v, np.clip(np.zeros(n), lo, hi),
+                                  jac=lambda v: H @ v - c, method="L-BFGS-B",
+                                  bounds=[(None if not np.isfinite(a) else a, None if not np.isfinite(b) else b)
+                                          for a, b in zip(lo, hi)],
+                                  options={"ftol": 1e-15, "gtol": 1e-12, "maxiter": 10000})
+    assert np.allclose(z, ref.x, atol=1e-6)
+    f = lambda v: 0.5 * v @ H @ v - c @ v
+    assert f(z) <= f(ref.x) + 1e-12
+
+
+def test_box_qp_diagonal_is_the_clamp():
+    rng = np.random.default_rng(1)
+    d = rng.uniform(0.5, 3.0, 4)
+    c = rng.normal(size=4) * 2
+    lo, hi = np.array([-0.3, -np.inf, -1.0, -0.2]), np.array([0.3, 0.5, np.inf, 0.1])
+    assert np.allclose(O.box_qp(np.diag(d), c, lo, hi), np.clip(c / d, lo, hi), atol=1e-14)
+
+
+def test_block_phi_step_with_diagonal_blocks_equals_row_step():
+    p = I.make_instance(6, 4, 1, seed=8, boxes=True, x0_dist="uniform", x_bound=0.6, u_bound=0.3)
+    rng = np.random.default_rng(2)
+    p.q = rng.uniform(0.5, 2.0, p.q.shape)
+    p.r = rng.uniform(0.5, 2.0, p.r.shape)
+    lay = O.Layout(p)
+    Psi, Lam = rng.normal(size=lay.nnz), rng.normal(size=lay.nnz) * 0.3
+    a, za = O.phi_step(lay, Psi, Lam, p.x0, p.rho)
+    b, zb = O.phi_step_block(lay, Psi, Lam, p.x0, p.rho)
+    assert np.allclose(a, b, atol=1e-12) and np.allclose(za, zb, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,T", [(3, 4), (4, 5)])
+def test_block_cost_admm_matches_riccati(n, T):
+    """d >= N-1, no boxes, full blocks Q_i, R_i: u(0) of the ADMM equals the
+    finite-horizon LQR gain with block-diagonal Q = diag(Q_i), R = diag(R_i)."""
+    p = I.with_block_costs(I.make_instance(n, T, n - 1, seed=21, boxes=False, x0_dist="normal"), seed=9)
+    A, B = p.dense_A(), p.dense_B()
+    Q = scipy.linalg.block_diag(*p.Q_blk)
+    R = scipy.linalg.block_diag(*p.R_blk)
+    u_ref = _riccati_u0(A, B, Q, R, T, p.x0.reshape(-1))
+    o = O.Oracle(p)
+    res = O.admm(o.lay, o.blocks, p.x0, max_iter=50000, eps_p=1e-11, eps_d=1e-11)
+    assert res.status == O.STATUS_CONVERGED
+    assert np.allclose(o.control(res).reshape(-1), u_ref, atol=1e-8)
+
+
+def test_block_cost_admm_matches_centralised_boxed_qp():
+    """Full blocks and boxes: the converged trajectory solves the centralised
+    QP min y^T W y over the locality-constrained affine set with the box, W
+    block-diagonal over (subsystem, slot); checked by the KKT conditions of
+    that QP at the ADMM solution (stationarity on the free set, multiplier
+    signs on the active box rows)."""
+    base = I.make_instance(4, 4, 1, seed=3, boxes=True, x0_dist="uniform", x_bound=1.0, u_bound=0.1)
+    base.x0 = 0.9 * base.x0
+    p = I.with_block_costs(base, seed=4)
+    lay, y0, G = _centralised_affine(p, p.x0)
+    U, S, _ = np.linalg.svd(G, full_matrices=False)
+    Bm = U[:, S > 1e-10 * S[0]]
+    W = np.zeros((lay.n_rows, lay.n_rows))
+    for i in range(p.n_sub):
+        for t in range(p.T):
+            rr = [O.global_row(p, i, t * p.nx + a) for a in range(p.nx)]
+            W[np.ix_(rr, rr)] = p.Q_blk[i]
+        for t in range(p.T - 1):
+            rr = [O.global_row(p, i, p.nx * p.T + t * p.nu + b) for b in range(p.nu)]
+            W[np.ix_(rr, rr)] = p.R_blk[i]
+    o = O.Oracle(p)
+    res = O.admm(o.lay, o.blocks, p.x0, max_iter=50000, eps_p=1e-10, eps_d=1e-10)
+    assert res.status == O.STATUS_CONVERGED
+    y = o.lay.trajectory(res.Phi, p.x0)
+    # y = y0 + Bm phi, feasible
+    phi = Bm.T @ (y - y0)
+    assert np.allclose(y0 + Bm @ phi, y, atol=1e-8)
+    assert np.all(y <= lay.hi + 1e-8) and np.all(y >= lay.lo - 1e-8)
+    # KKT: 2 Bm^T W y + Bm^T (mu_hi - mu_lo) = 0 with mu >= 0 on the active rows only
+    grad = 2 * Bm.T @ (W @ y)
+    at_hi = np.isfinite(lay.hi) & (y >= lay.hi - 1e-7)
+    at_lo = np.isfinite(lay.lo) & (y <= lay.lo + 1e-7)
+    assert (at_hi | at_lo).sum() >= 1, "the box must be active"
+    C = np.hstack([Bm[at_hi].T, -Bm[at_lo].T])
+    mu = np.linalg.lstsq(C, -grad, rcond=None)[0]
+    assert np.allclose(C @ mu, -grad, atol=1e-6)
+    assert np.all(mu >= -1e-6)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_block_phi_step_matches_slsqp_on_the_slot_problem(seed):
+    """One time slot of one subsystem, solved directly in the Phi entries:
+    min (Phi_s xh)^T C (Phi_s xh) + rho/2 ||Phi_s - V_s||_F^2 s.t. the box on
+    Phi_s xh, with SLSQP over all nx (or nu) rows of the slot at once; the block
+    Phi-step's rows must agree (this fixes the factor between the cost and the
+    penalty, which a converged solution alone does not see)."""
+    p = I.with_block_costs(I.make_instance(5, 4, 1, seed=seed, boxes=True, x0_dist="uniform",
+                                           x_bound=0.4, u_bound=0.2), seed=seed + 10, coupling=0.8)
+    rng = np.random.default_rng(seed)
+    lay = O.Layout(p)
+    Psi, Lam = rng.normal(size=lay.nnz) * 0.7, rng.normal(size=lay.nnz) * 0.3
+    Phi, _ = O.phi_step_block(lay, Psi, Lam, p.x0, p.rho)
+    V = Psi - Lam
+    xf = p.x0.reshape(-1)
+    i = 2
+    for rows, C in [([O.global_row(p, i, 1 * p.nx + a) for a in range(p.nx)], p.Q_blk[i]),
+                    ([O.global_row(p, i, p.nx * p.T + 0 * p.nu + b) for b in range(p.nu)], p.R_blk[i])]:
+        sel = [np.nonzero(lay.rows == r)[0] for r in rows]
+        cols = [lay.cols[e] for e in sel]
+        xh = [xf[c] for c in cols]
+        v = [V[e] for e in sel]
+        sizes = [len(e) for e in sel]
+
+        def unpack(theta):
+            out, o = [], 0
+            for k in sizes:
+                out.append(theta[o:o + k]); o += k
+            return out
+
+        def f(theta):
+            ph = unpack(theta)
+            z = np.array([ph[a] @ xh[a] for a in range(len(rows))])
+            return z @ C @ z + 0.5 * p.rho * sum(np.sum((ph[a] - v[a]) ** 2) for a in range(len(rows)))
+
+        cons = []
+        for a, r in enumerate(rows):
+            if np.isfinite(lay.hi[r]):
+                cons.append({"type": "ineq", "fun": (lambda th, a=a, r=r: lay.hi[r] - unpack(th)[a] @ xh[a])})
+                cons.append({"type": "ineq", "fun": (lambda th, a=a, r=r: unpack(th)[a] @ xh[a] - lay.lo[r])})
+        res = scipy.optimize.minimize(f, np.concatenate(v), method="SLSQP", constraints=cons,
+                                      options={"ftol": 1e-14, "maxiter": 2000})
+        assert res.success
+        got = np.concatenate([Phi[e] for e in sel])
+        assert np.allclose(got, res.x, atol=1e-6), (seed, rows)
+        assert f(got) <= res.fun + 1e-9
