@@ -75,6 +75,12 @@ typedef struct {
   double rho;               /* ADMM penalty (> 0) */
   double eps_p, eps_d;      /* Conv thresholds on the per-subsystem residuals */
   int32_t max_iter;         /* ADMM iteration cap (>= 1) */
+  /* Full cost blocks (Sec. II-A with non-diagonal Q_t = Q, R_t = R), or NULL:
+   * [n_sub][nx][nx] Q_i and [n_sub][nu][nu] R_i, row-major, symmetric positive
+   * definite; when given they replace q / r.  The Phi-step then solves, per
+   * subsystem and time slot, the box-QP of the slot's nx (or nu) rows exactly. */
+  const double *Q_blk;
+  const double *R_blk;
 } dlmpc_problem;
 
 /* Per-instance result of one MPC step. */
@@ -126,6 +132,8 @@ typedef struct {
 #define DLMPC_OPT_RESIDENCY 8     /* shared-memory residency during a step: 0 none (all streamed),
                                      1 compact iterate, Psi/Lambda and q, 2 (default) also N where
                                      it fits; replans */
+#define DLMPC_OPT_BLOCK_PHI 14    /* != 0: use the slot box-QP Phi-step even when every cost
+                                     block is diagonal (it is used whenever one is not) */
 #define DLMPC_OPT_COMPACT 13      /* != 0 (default): iterations after the first of a step carry the
                                      projected iterate as Psi = q + N t and Lambda = x_c lhat (the
                                      same iterates as Alg. 2, with the v = Psi + alpha x algebra of

@@ -41,6 +41,7 @@ OPT_GRAPH = 10
 OPT_LEARN_PLANT = 11
 OPT_TEST_SKIP_ARRIVAL = 12
 OPT_COMPACT = 13
+OPT_BLOCK_PHI = 14
 
 # Every entry point declared in include/dlmpc.h (checked by the tests).
 EXPORTED = [
@@ -66,7 +67,7 @@ class Problem_C(ctypes.Structure):
                 ("A_diag", _dp), ("A_off", _dp), ("B", _dp), ("q", _dp), ("r", _dp),
                 ("x_lo", _dp), ("x_hi", _dp), ("u_lo", _dp), ("u_hi", _dp),
                 ("rho", ctypes.c_double), ("eps_p", ctypes.c_double), ("eps_d", ctypes.c_double),
-                ("max_iter", ctypes.c_int32)]
+                ("max_iter", ctypes.c_int32), ("Q_blk", _dp), ("R_blk", _dp)]
 
 
 class Stats_C(ctypes.Structure):
@@ -210,6 +211,8 @@ class Solver:
         c.u_lo = _ptr(keep(p.u_lo, np.float64), ctypes.c_double)
         c.u_hi = _ptr(keep(p.u_hi, np.float64), ctypes.c_double)
         c.rho, c.eps_p, c.eps_d, c.max_iter = p.rho, p.eps_p, p.eps_d, p.max_iter
+        c.Q_blk = _ptr(keep(getattr(p, "Q_blk", None), np.float64), ctypes.c_double)
+        c.R_blk = _ptr(keep(getattr(p, "R_blk", None), np.float64), ctypes.c_double)
         return c
 
     def _check(self, rc: int) -> int:

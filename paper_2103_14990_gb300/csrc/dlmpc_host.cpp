@@ -24,7 +24,7 @@ namespace dlmpc {
 cudaError_t launch_factor(const FactorParams &p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_repack(const Item *scratch_items, const Item *items, int n_items, const float *src, float *dst,
                           cudaStream_t s);
-const void *sweep_kernel_ptr(int nx, int gt);
+const void *sweep_kernel_ptr(int nx, int gt, bool blk);
 int sweep_group_floats(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad, int max_kpad, int max_nmem);
 cudaStream_t mlp_stream(const dlmpc_mlp *mlp);
 cudaError_t launch_sweep(const Params &P, int gt, int grid, size_t smem, cudaStream_t s);
@@ -101,7 +101,8 @@ struct Instance {
   int n_sub = 0, T = 0, d = 0, sub_off = 0, item_off = 0;
   std::vector<int32_t> adj_ptr, adj_idx;
   std::vector<double> A_diag, A_off, B, q, r, x_lo, x_hi, u_lo, u_hi;
-  bool has_x = false, has_u = false;
+  std::vector<double> Qb, Rb;  // full cost blocks [n_sub][nx][nx], [n_sub][nu][nu] (diag(q), diag(r) if none given)
+  bool has_x = false, has_u = false, has_blk = false;
   double rho = 1, eps_p = 1e-4, eps_d = 1e-4;
   int max_iter = 1000;
   std::vector<std::vector<int32_t>> patch;  // local ids, ascending
@@ -135,6 +136,8 @@ struct dlmpc_ctx {
   int64_t resident_n_items = 0, resident_state_items = 0;
   int residency = 2;  // 0: nothing resident, 1: compact iterate, Psi/Lambda and q resident, 2: also N
   int compact = 1;    // iterations after the first of a launch on the compact iterate
+  bool block_cost = false;  // some instance has full cost blocks: slot box-QP Phi-step
+  int force_block = 0;      // DLMPC_OPT_BLOCK_PHI
   int trace = 0;
   std::vector<int32_t> grp_ptr, grp_items, cta_inst_ptr, cta_inst;
   // options
@@ -146,6 +149,7 @@ struct dlmpc_ctx {
   DevBuf<int32_t> d_members, d_rev, d_np, d_grp_ptr, d_grp_items, d_cta_inst_ptr, d_cta_inst, d_adj_ptr, d_adj_idx,
       d_inst_iters, d_err, d_inst_item_ptr, d_sub_off;
   DevBuf<int64_t> d_goff;
+  DevBuf<float> d_qblk2, d_rblk2;
   DevBuf<float> d_N, d_q, d_cp, d_psi, d_lam, d_phi, d_G0, d_G1, d_S, d_qw, d_rw, d_xlo, d_xhi, d_ulo, d_uhi, d_rho,
       d_epsp, d_epsd, d_item_r, d_item_s, d_x, d_u, d_xn;
   DevBuf<double> d_Adiag, d_Aoff, d_B;
@@ -168,10 +172,11 @@ struct dlmpc_ctx {
     bool stats;
     int plan, fixed, max_iter;
     bool phi, trace;
-    int compact;
+    int compact, block;
     bool operator==(const GraphKey &o) const {
       return x == o.x && u == o.u && xn == o.xn && warm == o.warm && stats == o.stats && plan == o.plan &&
-             fixed == o.fixed && max_iter == o.max_iter && phi == o.phi && trace == o.trace && compact == o.compact;
+             fixed == o.fixed && max_iter == o.max_iter && phi == o.phi && trace == o.trace && compact == o.compact &&
+             block == o.block;
     }
   };
   struct GraphEntry {
@@ -288,6 +293,34 @@ int validate(const dlmpc_problem &p, int nx, int nu, std::string &msg) {
   if (p.x_lo)
     for (int i = 0; i < p.n_sub * nx; ++i)
       if (!(p.x_lo[i] <= 0 && p.x_hi[i] >= 0)) { msg = "0 must lie in [x_lo, x_hi]"; return DLMPC_ERR_ARG; }
+  // full cost blocks: symmetric and positive definite (Cholesky must succeed)
+  for (int which = 0; which < 2; ++which) {
+    const double *blk = which == 0 ? p.Q_blk : p.R_blk;
+    const int n = which == 0 ? nx : nu;
+    if (!blk) continue;
+    for (int i = 0; i < p.n_sub; ++i) {
+      const double *M = blk + (size_t)i * n * n;
+      double L[kMaxNx * kMaxNx] = {0};
+      for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+          if (!(std::fabs(M[a * n + b] - M[b * n + a]) <= 1e-12 * (1.0 + std::fabs(M[a * n + b])))) {
+            msg = "Q_blk / R_blk must be symmetric";
+            return DLMPC_ERR_ARG;
+          }
+        }
+      for (int a = 0; a < n; ++a)
+        for (int b = 0; b <= a; ++b) {
+          double v = M[a * n + b];
+          for (int c = 0; c < b; ++c) v -= L[a * n + c] * L[b * n + c];
+          if (a == b) {
+            if (!(v > 0)) { msg = "Q_blk / R_blk must be positive definite"; return DLMPC_ERR_ARG; }
+            L[a * n + a] = std::sqrt(v);
+          } else {
+            L[a * n + b] = v / L[b * n + b];
+          }
+        }
+    }
+  }
   return 0;
 }
 
@@ -409,6 +442,19 @@ extern "C" int dlmpc_setup(const dlmpc_problem *probs, int32_t n_inst, void *str
     I.B.assign(p.B, p.B + (size_t)p.n_sub * nx * nu);
     I.q.assign(p.q, p.q + (size_t)p.n_sub * nx);
     I.r.assign(p.r, p.r + (size_t)p.n_sub * nu);
+    I.has_blk = p.Q_blk != nullptr || p.R_blk != nullptr;
+    I.Qb.assign((size_t)p.n_sub * nx * nx, 0.0);
+    I.Rb.assign((size_t)p.n_sub * nu * nu, 0.0);
+    for (int i = 0; i < p.n_sub; ++i) {
+      for (int a = 0; a < nx; ++a)
+        for (int b = 0; b < nx; ++b)
+          I.Qb[((size_t)i * nx + a) * nx + b] =
+              p.Q_blk ? p.Q_blk[((size_t)i * nx + a) * nx + b] : (a == b ? p.q[(size_t)i * nx + a] : 0.0);
+      for (int a = 0; a < nu; ++a)
+        for (int b = 0; b < nu; ++b)
+          I.Rb[((size_t)i * nu + a) * nu + b] =
+              p.R_blk ? p.R_blk[((size_t)i * nu + a) * nu + b] : (a == b ? p.r[(size_t)i * nu + a] : 0.0);
+    }
     I.has_x = p.x_lo != nullptr;
     I.has_u = p.u_lo != nullptr;
     if (I.has_x) {
@@ -510,7 +556,7 @@ namespace {
 int upload_static(dlmpc_ctx *ctx) {
   const int nx = ctx->nx, nu = ctx->nu;
   cudaStream_t s = ctx->stream;
-  std::vector<float> qw, rw, xlo, xhi, ulo, uhi, rho, epsp, epsd;
+  std::vector<float> qw, rw, xlo, xhi, ulo, uhi, rho, epsp, epsd, qblk2, rblk2;
   std::vector<double> Ad, Ao, Bm;
   std::vector<int32_t> aptr{0}, aidx, inst_item_ptr{0};
   for (const Instance &I : ctx->inst) {
@@ -529,6 +575,9 @@ int upload_static(dlmpc_ctx *ctx) {
       for (int e = I.adj_ptr[i]; e < I.adj_ptr[i + 1]; ++e) aidx.push_back(I.sub_off + I.adj_idx[e]);
       aptr.push_back((int32_t)aidx.size());
     }
+    for (double v : I.Qb) qblk2.push_back((float)(2.0 * v));
+    for (double v : I.Rb) rblk2.push_back((float)(2.0 * v));
+    ctx->block_cost = ctx->block_cost || I.has_blk;
     Ad.insert(Ad.end(), I.A_diag.begin(), I.A_diag.end());
     Ao.insert(Ao.end(), I.A_off.begin(), I.A_off.end());
     Bm.insert(Bm.end(), I.B.begin(), I.B.end());
@@ -538,6 +587,8 @@ int upload_static(dlmpc_ctx *ctx) {
     inst_item_ptr.push_back(I.item_off + I.n_sub);
   }
   CK(upload(ctx->d_qw, qw, s), "upload qw");
+  CK(upload(ctx->d_qblk2, qblk2, s), "upload Q blocks");
+  CK(upload(ctx->d_rblk2, rblk2, s), "upload R blocks");
   CK(upload(ctx->d_rw, rw, s), "upload rw");
   CK(upload(ctx->d_xlo, xlo, s), "upload xlo");
   CK(upload(ctx->d_xhi, xhi, s), "upload xhi");
@@ -619,8 +670,11 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
   CK(cudaGetDevice(&dev), "cudaGetDevice");
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
   CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-  const void *fn = sweep_kernel_ptr(nx, gt);
+  const void *fn = sweep_kernel_ptr(nx, gt, false);
   if (!fn) return ctx->fail(DLMPC_ERR_ARG, "no sweep kernel for this nx / group size");
+  const void *fn_blk = sweep_kernel_ptr(nx, gt, true);  // full cost blocks (64 and 128 threads)
+  if (ctx->block_cost && !fn_blk)
+    return ctx->fail(DLMPC_ERR_ARG, "full cost blocks need 64 or 128 threads per group");
   cudaFuncAttributes fa{};
   CK(cudaFuncGetAttributes(&fa, fn), "cudaFuncGetAttributes");
   const int64_t budget = ((int64_t)smem_optin - (int64_t)fa.sharedSizeBytes - 64) / 4;  // floats
@@ -734,6 +788,7 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
   ctx->smem = (size_t)((int64_t)ng * ctx->grp_floats + cta_floats + used_max) * 4;
   ++ctx->plan_version;
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem), "smem attr");
+  if (fn_blk) CK(cudaFuncSetAttribute(fn_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem), "smem attr");
   int occ = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, gt * ng, ctx->smem), "occupancy");
   if (occ < 1 || grid > occ * sms) return ctx->fail(DLMPC_ERR_ARG, "sweep kernel cannot be co-resident");
@@ -976,6 +1031,9 @@ Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_d
   P.trace = ctx->trace ? ctx->d_trace.p : nullptr;
   P.skip_arrival_cta = ctx->skip_arrival_cta;
   P.compact = ctx->compact;
+  P.block_cost = (ctx->block_cost || ctx->force_block) ? 1 : 0;
+  P.qblk2 = ctx->d_qblk2.p;
+  P.rblk2 = ctx->d_rblk2.p;
   P.cpst = ctx->d_cp.p;
   return P;
 }
@@ -1005,7 +1063,7 @@ int enqueue_step(dlmpc_ctx *ctx, const Params &P, bool with_stats, bool events, 
 // pointers and options.
 int graph_step(dlmpc_ctx *ctx, const Params &P, bool with_stats) {
   dlmpc_ctx::GraphKey key{P.x, P.u, P.x_next, P.warm, with_stats, ctx->plan_version, P.fixed_iters, P.max_iter,
-                          P.Phi != nullptr, P.trace != nullptr, P.compact};
+                          P.Phi != nullptr, P.trace != nullptr, P.compact, P.block_cost};
   for (auto &ge : ctx->graphs)
     if (ge.key == key) {
       CK(cudaGraphLaunch(ge.exec, ctx->stream), "cudaGraphLaunch");
@@ -1269,6 +1327,7 @@ extern "C" int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value) {
     case DLMPC_OPT_LEARN_PLANT: ctx->learn_plant = value != 0; return 0;
     case DLMPC_OPT_TEST_SKIP_ARRIVAL: ctx->skip_arrival_cta = (int)value; return 0;
     case DLMPC_OPT_COMPACT: ctx->compact = value != 0; return 0;
+    case DLMPC_OPT_BLOCK_PHI: ctx->force_block = value != 0; return 0;
     case DLMPC_OPT_RESIDENCY: {
       if (!(value >= 0 && value <= 2)) return ctx->fail(DLMPC_ERR_ARG, "residency must be 0, 1 or 2");
       ctx->residency = (int)value;
@@ -1370,6 +1429,7 @@ extern "C" int dlmpc_run_variant(dlmpc_ctx *ctx, int32_t variant, const float *x
   cudaStream_t s = ctx->stream;
   for (const Item &it : ctx->items)
     if (it.k > 256) return ctx->fail(DLMPC_ERR_ARG, "variants need null spaces of dimension <= 256");
+  if (ctx->block_cost) return ctx->fail(DLMPC_ERR_ARG, "the paper variants take diagonal cost weights only");
   if (!ctx->d_phi.p || ctx->d_phi.n != (size_t)ctx->state_floats) {
     CK(ctx->d_phi.alloc(ctx->state_floats), "alloc Phi");
     CK(cudaMemsetAsync(ctx->d_phi.p, 0, ctx->state_floats * 4, s), "memset");

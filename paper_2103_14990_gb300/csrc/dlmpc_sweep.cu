@@ -49,8 +49,9 @@ constexpr int kRowRecord = 8;
 
 // Floats of one patch-member record: exchange read offset, |Patch|, 1/s (0
 // when s = 0), exchange write base, then x[nx], rho/(rho + 2 q s)[nx],
-// x_lo[nx], x_hi[nx], rho/(rho + 2 r s)[nu], u_lo[nu], u_hi[nu].
-__host__ __device__ inline int member_record(int nx, int nu) { return 4 + 4 * nx + 3 * nu; }
+// x_lo[nx], x_hi[nx], rho/(rho + 2 r s)[nu], u_lo[nu], u_hi[nu], 2 Q_m
+// [nx][nx], 2 R_m [nu][nu].
+__host__ __device__ inline int member_record(int nx, int nu) { return 4 + 4 * nx + 3 * nu + nx * nx + nu * nu; }
 
 // Float offsets inside one group region; the host uses the same function.
 __host__ __device__ inline GroupLayout group_layout(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad,
@@ -135,6 +136,9 @@ __device__ __forceinline__ void fill_wave(const Params &P, const int *items, int
         rec[4 + 4 * NX + P.nu + bb] = P.ulo[m * P.nu + bb];
         rec[4 + 4 * NX + 2 * P.nu + bb] = P.uhi[m * P.nu + bb];
       }
+      float *blk = rec + 4 + 4 * NX + 3 * P.nu;
+      for (int e2 = 0; e2 < NX * NX; ++e2) blk[e2] = P.qblk2[(int64_t)m * NX * NX + e2];
+      for (int e2 = 0; e2 < P.nu * P.nu; ++e2) blk[NX * NX + e2] = P.rblk2[(int64_t)m * P.nu * P.nu + e2];
     }
   }
   group_sync(g, GT);
@@ -246,6 +250,143 @@ __device__ __forceinline__ void phi_rows(const Params &P, const Item &it, const 
     }
     phi_row(P, p, it.dred, ia.w, ca, w, alpha_out);
     if (two) phi_row(P, p2, it.dred, ib.w, cb, w2, alpha_out);
+  }
+}
+
+// argmin 1/2 z^T (C + cd I) z - cd w^T z  s.t.  lo <= z <= hi  (n <= kMaxQP,
+// C symmetric positive semi-definite, cd > 0): every component free, at lo or
+// at hi (finite bounds only); the free part solves its linear system
+// (Gaussian elimination, the matrix is positive definite), and among the
+// feasible candidates the one of least objective is the optimum (the optimum
+// of a strictly convex QP is one of them, and no feasible point is lower).
+constexpr int kMaxQP = 4;
+
+__device__ __forceinline__ void slot_box_qp(const float *C, float cd, const float *w, const float *lo,
+                                            const float *hi, int n, float *z_out) {
+  float best = INFINITY;
+  int npat = 1;
+  for (int a = 0; a < n; ++a) npat *= 3;
+  for (int pat = 0; pat < npat; ++pat) {
+    int d[kMaxQP];
+    bool ok = true;
+    int rem = pat;
+#pragma unroll
+    for (int a = 0; a < kMaxQP; ++a) {
+      d[a] = 0;
+      if (a < n) {
+        d[a] = rem % 3;
+        rem /= 3;
+        if ((d[a] == 1 && !(lo[a] > -INFINITY)) || (d[a] == 2 && !(hi[a] < INFINITY))) ok = false;
+      }
+    }
+    if (!ok) continue;
+    float z[kMaxQP], M[kMaxQP][kMaxQP + 1];
+    int fi[kMaxQP];
+    int m = 0;
+#pragma unroll
+    for (int a = 0; a < kMaxQP; ++a) {
+      z[a] = 0.f;
+      if (a < n && d[a] != 0) z[a] = d[a] == 1 ? lo[a] : hi[a];
+    }
+#pragma unroll
+    for (int a = 0; a < kMaxQP; ++a)
+      if (a < n && d[a] == 0) fi[m++] = a;
+    // M [m x m | rhs]: (C + cd I)_FF z_F = cd w_F - (C)_FA z_A
+    for (int i = 0; i < m; ++i) {
+      const int a = fi[i];
+      float rhs = cd * w[a];
+      for (int b = 0; b < n; ++b)
+        if (d[b] != 0) rhs -= C[a * n + b] * z[b];
+      for (int j = 0; j < m; ++j) M[i][j] = C[a * n + fi[j]] + (i == j ? cd : 0.f);
+      M[i][m] = rhs;
+    }
+    for (int i = 0; i < m; ++i) {
+      const float inv = 1.f / M[i][i];
+      for (int r = i + 1; r < m; ++r) {
+        const float f = M[r][i] * inv;
+        for (int j = i; j <= m; ++j) M[r][j] -= f * M[i][j];
+      }
+    }
+    for (int i = m - 1; i >= 0; --i) {
+      float v = M[i][m];
+      for (int j = i + 1; j < m; ++j) v -= M[i][j] * z[fi[j]];
+      z[fi[i]] = v / M[i][i];
+    }
+    for (int i = 0; i < m && ok; ++i) {
+      const int a = fi[i];
+      const float tol_lo = 1e-5f * fmaxf(1.f, fabsf(lo[a])), tol_hi = 1e-5f * fmaxf(1.f, fabsf(hi[a]));
+      if (z[a] < lo[a] - tol_lo || z[a] > hi[a] + tol_hi) ok = false;
+      z[a] = fminf(fmaxf(z[a], lo[a]), hi[a]);
+    }
+    if (!ok) continue;
+    float obj = 0.f;
+    for (int a = 0; a < n; ++a) {
+      float hz = cd * z[a];
+      for (int b = 0; b < n; ++b) hz = fmaf(C[a * n + b], z[b], hz);
+      obj = fmaf(z[a], 0.5f * hz - cd * w[a], obj);
+    }
+    if (obj < best) {
+      best = obj;
+      for (int a = 0; a < n; ++a) z_out[a] = z[a];
+    }
+  }
+}
+
+// Phi-comp with full cost blocks Q_i, R_i: the rows of one member at one time
+// slot (its nx state rows or its nu input rows, consecutive in reduced order)
+// share x_hat and are solved together: w per row from the row sums, then
+// min z^T C z + rho/(2 s) ||z - w||^2 over the slot's box (slot_box_qp with
+// H = 2 C + (rho/s) I), alpha = (z - w)/s per row.  One thread per slot.
+template <int NX>
+__device__ void phi_slots(const Params &P, const Item &it, const float *tab, const float *rt, const float *Gcur,
+                          float *alpha_out, float rho, int gt, int GT) {
+  const int T = it.T, r_sub = it.r_sub, rs_red = r_sub - NX, dred = it.dred, nu = P.nu;
+  const int MT = member_record(NX, nu);
+  const int per = 2 * T - 1;  // T state slots, T - 1 input slots per member
+  for (int g = gt; g < it.n_mem * per; g += GT) {
+    const int mpos = small_div(g, per), kk = g - mpos * per;
+    int p0, n;
+    const float *rec = tab + mpos * MT;
+    const float *C = rec + 4 + 4 * NX + 3 * nu;
+    if (kk < T) {
+      n = NX;
+      p0 = kk == 0 ? dred + mpos * NX : mpos * rs_red + (kk - 1) * NX;
+    } else {
+      n = nu;
+      p0 = mpos * rs_red + (T - 1) * NX + (kk - T) * nu;
+      C += NX * NX;
+    }
+    float w[kMaxQP], lo[kMaxQP], hi[kMaxQP], z[kMaxQP];
+    int aux[kMaxQP];
+#pragma unroll
+    for (int a = 0; a < kMaxQP; ++a) {
+      w[a] = 0.f;
+      lo[a] = -INFINITY;
+      hi[a] = INFINITY;
+      aux[a] = -1;
+      if (a < n) {
+        const int p = p0 + a;
+        const int4 ia = *reinterpret_cast<const int4 *>(rt + p * kRowRecord);
+        const float4 ca = *reinterpret_cast<const float4 *>(rt + p * kRowRecord + 4);
+        float s = 0.f;
+        for (int j = 0; j < ia.y; ++j) s += __ldcg(Gcur + ia.x + j * r_sub);
+        w[a] = s;
+        lo[a] = ca.y;
+        hi[a] = ca.z;
+        aux[a] = ia.w;
+      }
+      z[a] = w[a];
+    }
+    const float inv_s = rec[2];
+    if (inv_s > 0.f) slot_box_qp(C, rho * inv_s, w, lo, hi, n, z);
+#pragma unroll
+    for (int a = 0; a < kMaxQP; ++a) {
+      if (a < n) {
+        const int p = p0 + a;
+        alpha_out[p] = inv_s > 0.f ? (z[a] - w[a]) * inv_s : 0.f;
+        if (aux[a] >= 0 && p < dred) P.u[aux[a]] = z[a];
+      }
+    }
   }
 }
 
@@ -688,7 +829,9 @@ __device__ __forceinline__ bool sweep_barrier(const Params &P, unsigned e, unsig
   return ok_sh != 0;
 }
 
-template <int NX, int GT>
+// BLK: the Phi-step takes full cost blocks (phi_slots); a separate
+// instantiation keeps that solver out of the diagonal kernel's registers.
+template <int NX, int GT, bool BLK>
 __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
   extern __shared__ __align__(16) float sm[];
   const int tid = threadIdx.x;
@@ -817,7 +960,11 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
       for (int wi = 0; wi < wn; ++wi) {
         const Item &it = cached_item(G.icache, wi);
         if (!lact[it.lslot]) continue;
-        phi_rows<GT>(P, it, G.rtab + wi * P.max_dcol * kRowRecord, Gcur, G.alpha + wi * P.max_dcol, gt);
+        if constexpr (BLK)
+          phi_slots<NX>(P, it, G.mtab + wi * P.max_nmem * MT, G.rtab + wi * P.max_dcol * kRowRecord, Gcur,
+                        G.alpha + wi * P.max_dcol, cached_extra(G.icache, wi)[0], gt, GT);
+        else
+          phi_rows<GT>(P, it, G.rtab + wi * P.max_dcol * kRowRecord, Gcur, G.alpha + wi * P.max_dcol, gt);
       }
       group_sync(g, GT);
       if (w0 == gi0) trace_point(P, iter, 1);
@@ -911,18 +1058,24 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
 // host-side launch helpers
 // ---------------------------------------------------------------------------
 
-template <int NX, int GT>
+template <int NX, int GT, bool BLK>
 static const void *sweep_fn() {
-  return reinterpret_cast<const void *>(&sweep_kernel<NX, GT>);
+  return reinterpret_cast<const void *>(&sweep_kernel<NX, GT, BLK>);
 }
 
-const void *sweep_kernel_ptr(int nx, int gt) {
-#define DLMPC_SWEEP_CASE(NXV)                    \
-  case NXV:                                      \
-    if (gt == 64) return sweep_fn<NXV, 64>();    \
-    if (gt == 96) return sweep_fn<NXV, 96>();    \
-    if (gt == 128) return sweep_fn<NXV, 128>();  \
-    if (gt == 256) return sweep_fn<NXV, 256>();  \
+// blk: the full-cost-block variant, built for 64 and 128 threads per group
+const void *sweep_kernel_ptr(int nx, int gt, bool blk) {
+#define DLMPC_SWEEP_CASE(NXV)                                 \
+  case NXV:                                                   \
+    if (blk) {                                                \
+      if (gt == 64) return sweep_fn<NXV, 64, true>();         \
+      if (gt == 128) return sweep_fn<NXV, 128, true>();       \
+      return nullptr;                                         \
+    }                                                         \
+    if (gt == 64) return sweep_fn<NXV, 64, false>();          \
+    if (gt == 96) return sweep_fn<NXV, 96, false>();          \
+    if (gt == 128) return sweep_fn<NXV, 128, false>();        \
+    if (gt == 256) return sweep_fn<NXV, 256, false>();        \
     return nullptr;
   switch (nx) {
     DLMPC_SWEEP_CASE(1)
@@ -939,7 +1092,7 @@ int sweep_group_floats(int nx, int nu, int gt, int wave, int max_dcol, int max_d
 }
 
 cudaError_t launch_sweep(const Params &P, int gt, int grid, size_t smem, cudaStream_t s) {
-  const void *fn = sweep_kernel_ptr(P.nx, gt);
+  const void *fn = sweep_kernel_ptr(P.nx, gt, P.block_cost != 0);
   if (!fn) return cudaErrorInvalidValue;
   Params pc = P;
   void *args[] = {&pc};

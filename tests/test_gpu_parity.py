@@ -329,3 +329,81 @@ def test_paper_variants_match_oracle(name, variant, torch):
     phi, psi, lam = [a.cpu().numpy() for a in s.get_state(phi=True)]
     assert rel(psi, ref.Psi) <= REL and rel(lam, ref.Lam) <= REL and rel(phi, ref.Phi) <= REL
     s.close()
+
+
+# --------------------------------------------------------------------------
+# Full cost blocks Q_i, R_i (slot box-QP Phi-step)
+# --------------------------------------------------------------------------
+
+BLOCK = {
+    "chain16_T10_d3_box_blk": lambda: I.with_block_costs(SMALL["chain16_T10_d3_box"](), seed=31),
+    "grid5x5_T6_d2_box_blk": lambda: I.with_block_costs(SMALL["grid5x5_T6_d2_box"](), seed=32),
+    "chain10_blk": lambda: I.with_block_costs(I.chain10(), seed=33),
+}
+
+
+@pytest.mark.parametrize("name", list(BLOCK))
+@pytest.mark.parametrize("K", [1, 7, 60])
+def test_block_cost_fixed_iterations_parity(name, K, torch):
+    """Phi, Psi, Lambda and u after K iterations against the oracle's block
+    Phi-step (full form with Phi export, and the compact iterate)."""
+    p = BLOCK[name]()
+    o = O.Oracle(p)
+    ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=K)
+    s = gpu_solver([p], torch)
+    rc, st, phi, psi, lam, u, xn = run_fixed(s, torch, p.x0, K)
+    assert rel(psi, ref.Psi) <= REL and rel(phi, ref.Phi) <= REL
+    assert rel(lam, ref.Lam) <= REL or np.linalg.norm(ref.Lam) < 1e-6
+    u_ref = o.control(ref)
+    assert rel(u, u_ref) <= REL or np.max(np.abs(u - u_ref)) < 1e-7
+    rc, st, _, psi2, lam2, u2, _ = run_fixed(s, torch, p.x0, K, export=False)
+    assert rel(psi2, ref.Psi) <= REL
+    assert rel(u2, u_ref) <= REL or np.max(np.abs(u2 - u_ref)) < 1e-7
+    s.close()
+
+
+def test_block_cost_stopped_closed_loop(torch):
+    import paper_2103_14990_gb300 as pkg
+    p = BLOCK["chain10_blk"]()
+    o = O.Oracle(p)
+    xs, us, its, _ = o.run_mpc(p.mpc_steps, warm="previous")
+    s = gpu_solver([p], torch)
+    worst = 0.0
+    for tau in range(p.mpc_steps):
+        x = torch.tensor(xs[tau].astype(np.float32), device="cuda")
+        u = torch.zeros(p.n_sub, 1, device="cuda")
+        rc, st = s.step(x, u, None, warm=pkg.WARM_PREVIOUS if tau > 0 else pkg.WARM_COLD)
+        assert st[0]["status"] == 0
+        assert abs(st[0]["iters"] - its[tau]) <= max(3, 0.02 * its[tau])
+        worst = max(worst, rel(u.cpu().numpy(), us[tau]))
+    assert worst <= 5 * REL
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["chain16_T10_d3_box", "grid5x5_T6_d2_box"])
+def test_block_phi_on_diagonal_costs_matches_row_phi(name, torch):
+    """The slot box-QP with diagonal blocks is the per-row closed form."""
+    import paper_2103_14990_gb300 as pkg
+    p = SMALL[name]()
+    s = gpu_solver([p], torch)
+    _, _, phi_a, psi_a, _, u_a, _ = run_fixed(s, torch, p.x0, 30)
+    s.set_option(pkg.OPT_BLOCK_PHI, 1)
+    _, _, phi_b, psi_b, _, u_b, _ = run_fixed(s, torch, p.x0, 30)
+    assert rel(phi_b, phi_a) <= 1e-5 and rel(psi_b, psi_a) <= 1e-5
+    assert rel(u_b, u_a) <= 1e-5 or np.max(np.abs(u_a - u_b)) < 1e-7
+    s.close()
+
+
+def test_block_cost_validation(torch):
+    import paper_2103_14990_gb300 as pkg
+    p = BLOCK["chain10_blk"]()
+    bad = p.Q_blk.copy()
+    bad[3] = np.array([[1.0, 2.0], [2.0, 1.0]])          # indefinite
+    import dataclasses
+    with pytest.raises(pkg.DlmpcError):
+        pkg.Solver([dataclasses.replace(p, Q_blk=bad)])
+    s = gpu_solver([p], torch)
+    x = torch.tensor(p.x0.astype(np.float32), device="cuda")
+    with pytest.raises(pkg.DlmpcError):
+        s.run_variant(0, x, 2)                            # the paper variants take diagonal weights
+    s.close()
