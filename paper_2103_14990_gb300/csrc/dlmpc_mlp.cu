@@ -3,8 +3,9 @@
 //     h1 = GELU(x W1 + b1), h2 = GELU(h1 W2 + b2), y = h2 W3 + b3
 // with BF16 operands and FP32 accumulation on the tensor cores
 // (mma.sync m16n8k16), FP32 master weights and AdamW.  The GEMMs here are
-// small (n x 14 x 256, n x 256 x 256, n x 256 x d_out); one generic tiled
-// kernel serves the forward and both backward products.
+// small (n x d_in x 256, n x 256 x 256, n x 256 x d_out); one generic tiled
+// kernel serves the forward (bias and GELU fused into its epilogue) and both
+// backward products.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -19,8 +20,8 @@
 namespace {
 
 constexpr int kTile = 64;   // CTA tile (M and N)
-constexpr int kKStep = 16;  // K per mma
-constexpr int kLd = 24;     // padded row (bf16) of a shared tile: conflict-free 32-bit fragment loads
+constexpr int kKc = 32;     // K per staged chunk (two m16n8k16 steps)
+constexpr int kLd = 40;     // padded row (bf16) of a shared tile: conflict-free 32-bit fragment loads
 
 __device__ __forceinline__ uint32_t pack2(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
@@ -33,18 +34,93 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+__device__ __forceinline__ float gelu(float x);
+
+// One operand chunk (kTile rows of the M or N side x kKc of K) as 8 pairs of
+// bf16 per thread, read along the source's contiguous dimension.  kcont: the
+// source is contiguous along K (src[r * ld + k]); otherwise along the row
+// index (src[k * ld + r]).  Out-of-range elements read as zero.
+struct Chunk {
+  uint32_t v[8];
+};
+
+__device__ __forceinline__ uint32_t pair_bits(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void load_chunk(Chunk &c, const __nv_bfloat16 *src, int ld, bool kcont, bool pairs,
+                                           int r0, int rmax, int k0, int kmax, int tid) {
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int e = tid + 128 * i;
+    int r, k, r2, k2;
+    if (kcont) {
+      r = r0 + (e >> 4);
+      k = k0 + 2 * (e & 15);
+      r2 = r;
+      k2 = k + 1;
+    } else {
+      k = k0 + (e >> 5);
+      r = r0 + 2 * (e & 31);
+      k2 = k;
+      r2 = r + 1;
+    }
+    const bool in1 = r < rmax && k < kmax, in2 = r2 < rmax && k2 < kmax;
+    const int64_t o1 = kcont ? (int64_t)r * ld + k : (int64_t)k * ld + r;
+    if (pairs && in1 && in2) {
+      c.v[i] = *reinterpret_cast<const uint32_t *>(src + o1);
+    } else {
+      const __nv_bfloat16 x1 = in1 ? src[o1] : zero;
+      const __nv_bfloat16 x2 = in2 ? src[o1 + 1] : zero;
+      c.v[i] = pair_bits(x1, x2);
+    }
+  }
+}
+
+// Writes a chunk into the shared tile T[row][k] (row = M or N index).
+__device__ __forceinline__ void store_chunk(const Chunk &c, __nv_bfloat16 (*T)[kLd], bool kcont, int tid) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int e = tid + 128 * i;
+    if (kcont) {
+      *reinterpret_cast<uint32_t *>(&T[e >> 4][2 * (e & 15)]) = c.v[i];
+    } else {
+      const int kk = e >> 5, rr = 2 * (e & 31);
+      T[rr][kk] = __ushort_as_bfloat16((unsigned short)(c.v[i] & 0xffffu));
+      T[rr + 1][kk] = __ushort_as_bfloat16((unsigned short)(c.v[i] >> 16));
+    }
+  }
+}
+
 // C[M x N] (+)= op(A)[M x K] op(B)[K x N]; op(A) = A (A[m*lda+k]) or A^T
 // (A[k*lda+m]); op(B) = B (B[k*ldb+n]) or B^T (B[n*ldb+k]).  BF16 inputs,
-// FP32 accumulate and output.  128 threads, 4 warps of 32x32.
+// FP32 accumulate.  128 threads, 4 warps of 32x32; K staged in chunks of 32
+// through shared memory, the next chunk loaded into registers while the
+// current one is multiplied.  Epilogue: epi = 0 stores (or adds) C;
+// epi = 1 adds bias[n], stores C (pre-activation) and act = BF16(GELU(C));
+// epi = 2 adds bias[n], stores C and out = C * scale[n] + shift[n] (or C
+// when scale is null) when out is given.
+struct Epilogue {
+  int epi;
+  const float *bias;
+  __nv_bfloat16 *act;
+  float *out;
+  const float *scale, *shift;
+};
+
 __global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const __nv_bfloat16 *A, int lda, int ta,
                                                         const __nv_bfloat16 *B, int ldb, int tb, float *C, int ldc,
-                                                        int accumulate) {
+                                                        int accumulate, Epilogue ep) {
   __shared__ __align__(16) __nv_bfloat16 As[kTile][kLd];  // [m][k]
   __shared__ __align__(16) __nv_bfloat16 Bs[kTile][kLd];  // [n][k]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int bm = blockIdx.y * kTile, bn = blockIdx.x * kTile;
   const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const bool a_k = ta == 0, b_k = tb != 0;  // operand contiguous along K
+  const bool a_pairs = (lda % 2) == 0 && (reinterpret_cast<uintptr_t>(A) & 3) == 0;
+  const bool b_pairs = (ldb % 2) == 0 && (reinterpret_cast<uintptr_t>(B) & 3) == 0;
   float acc[2][4][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -52,33 +128,33 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, con
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-  const __nv_bfloat16 zero = __float2bfloat16(0.f);
-  for (int k0 = 0; k0 < K; k0 += kKStep) {
-    for (int e = tid; e < kTile * kKStep; e += 128) {
-      const int r = e / kKStep, kk = e % kKStep;
-      const int gm = bm + r, gk = k0 + kk;
-      __nv_bfloat16 av = zero;
-      if (gm < M && gk < K) av = ta ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
-      As[r][kk] = av;
-      const int gn = bn + r;
-      __nv_bfloat16 bv = zero;
-      if (gn < N && gk < K) bv = tb ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
-      Bs[r][kk] = bv;
-    }
+  Chunk ca, cb;
+  load_chunk(ca, A, lda, a_k, a_pairs, bm, M, 0, K, tid);
+  load_chunk(cb, B, ldb, b_k, b_pairs, bn, N, 0, K, tid);
+  for (int k0 = 0; k0 < K; k0 += kKc) {
+    store_chunk(ca, As, a_k, tid);
+    store_chunk(cb, Bs, b_k, tid);
     __syncthreads();
+    if (k0 + kKc < K) {
+      load_chunk(ca, A, lda, a_k, a_pairs, bm, M, k0 + kKc, K, tid);
+      load_chunk(cb, B, ldb, b_k, b_pairs, bn, N, k0 + kKc, K, tid);
+    }
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int m0 = wm + 16 * i;
-      const uint32_t a0 = pack2(&As[m0 + g][2 * t]);
-      const uint32_t a1 = pack2(&As[m0 + g + 8][2 * t]);
-      const uint32_t a2 = pack2(&As[m0 + g][2 * t + 8]);
-      const uint32_t a3 = pack2(&As[m0 + g + 8][2 * t + 8]);
+    for (int ks = 0; ks < kKc; ks += 16) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n0 = wn + 8 * j;
-        const uint32_t b0 = pack2(&Bs[n0 + g][2 * t]);
-        const uint32_t b1 = pack2(&Bs[n0 + g][2 * t + 8]);
-        mma_bf16(acc[i][j], a0, a1, a2, a3, b0, b1);
+      for (int i = 0; i < 2; ++i) {
+        const int m0 = wm + 16 * i;
+        const uint32_t a0 = pack2(&As[m0 + g][ks + 2 * t]);
+        const uint32_t a1 = pack2(&As[m0 + g + 8][ks + 2 * t]);
+        const uint32_t a2 = pack2(&As[m0 + g][ks + 2 * t + 8]);
+        const uint32_t a3 = pack2(&As[m0 + g + 8][ks + 2 * t + 8]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int n0 = wn + 8 * j;
+          const uint32_t b0 = pack2(&Bs[n0 + g][ks + 2 * t]);
+          const uint32_t b1 = pack2(&Bs[n0 + g][ks + 2 * t + 8]);
+          mma_bf16(acc[i][j], a0, a1, a2, a3, b0, b1);
+        }
       }
     }
     __syncthreads();
@@ -92,8 +168,16 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, con
         const int m = bm + wm + 16 * i + g + ((e >> 1) << 3);
         const int n = bn + wn + 8 * j + 2 * t + (e & 1);
         if (m < M && n < N) {
-          float *dst = C + (int64_t)m * ldc + n;
-          *dst = accumulate ? *dst + acc[i][j][e] : acc[i][j][e];
+          const int64_t o = (int64_t)m * ldc + n;
+          float v = acc[i][j][e];
+          if (ep.epi == 0) {
+            C[o] = accumulate ? C[o] + v : v;
+          } else {
+            v += ep.bias[n];
+            C[o] = v;
+            if (ep.epi == 1) ep.act[o] = __float2bfloat16(gelu(v));
+            else if (ep.out) ep.out[o] = ep.scale ? v * ep.scale[n] + ep.shift[n] : v;
+          }
         }
       }
 }
@@ -106,20 +190,6 @@ __device__ __forceinline__ float gelu_grad(float x) {
 __global__ void to_bf16_kernel(const float *in, __nv_bfloat16 *out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = __float2bfloat16(in[i]);
-}
-
-// pre += bias (row-broadcast); act = GELU(pre) as BF16 (or, if act == null,
-// out_f32 = pre * scale + shift per column).
-__global__ void bias_act_kernel(float *pre, const float *bias, int n, int d, __nv_bfloat16 *act, float *out,
-                                const float *scale, const float *shift) {
-  const int64_t total = (int64_t)n * d;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % d);
-    const float v = pre[i] + bias[c];
-    pre[i] = v;
-    if (act) act[i] = __float2bfloat16(gelu(v));
-    if (out) out[i] = scale ? v * scale[c] + shift[c] : v;
-  }
 }
 
 // dy = 2 (y - t) / (n d), loss partial sums of (y - t)^2 (FP64 atomics).
@@ -254,9 +324,10 @@ int ensure_batch(dlmpc_mlp *mlp, int n) {
 }
 
 int gemm(dlmpc_mlp *mlp, int M, int N, int K, const __nv_bfloat16 *A, int lda, int ta, const __nv_bfloat16 *B,
-         int ldb, int tb, float *C, int ldc, int acc) {
+         int ldb, int tb, float *C, int ldc, int acc, Epilogue ep = Epilogue{0, nullptr, nullptr, nullptr, nullptr,
+                                                                                nullptr}) {
   dim3 grid((N + kTile - 1) / kTile, (M + kTile - 1) / kTile);
-  gemm_bf16_kernel<<<grid, 128, 0, mlp->stream>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc, acc);
+  gemm_bf16_kernel<<<grid, 128, 0, mlp->stream>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc, acc, ep);
   MK(cudaGetLastError(), "gemm_bf16_kernel");
   return 0;
 }
@@ -269,15 +340,16 @@ int forward(dlmpc_mlp *mlp, const float *x, int n, float *out, bool denorm) {
   cudaStream_t s = mlp->stream;
   const int I = mlp->d_in, H = mlp->hid, O = mlp->d_out;
   to_bf16_kernel<<<blocks_for((int64_t)n * I), 256, 0, s>>>(x, mlp->x_bf, (int64_t)n * I);
-  if ((rc = gemm(mlp, n, H, I, mlp->x_bf, I, 0, mlp->w_bf + mlp->oW1, H, 0, mlp->h1, H, 0))) return rc;
-  bias_act_kernel<<<blocks_for((int64_t)n * H), 256, 0, s>>>(mlp->h1, mlp->w + mlp->ob1, n, H, mlp->h1_bf, nullptr,
-                                                             nullptr, nullptr);
-  if ((rc = gemm(mlp, n, H, H, mlp->h1_bf, H, 0, mlp->w_bf + mlp->oW2, H, 0, mlp->h2, H, 0))) return rc;
-  bias_act_kernel<<<blocks_for((int64_t)n * H), 256, 0, s>>>(mlp->h2, mlp->w + mlp->ob2, n, H, mlp->h2_bf, nullptr,
-                                                             nullptr, nullptr);
-  if ((rc = gemm(mlp, n, O, H, mlp->h2_bf, H, 0, mlp->w_bf + mlp->oW3, O, 0, mlp->y, O, 0))) return rc;
-  bias_act_kernel<<<blocks_for((int64_t)n * O), 256, 0, s>>>(mlp->y, mlp->w + mlp->ob3, n, O, nullptr, out,
-                                                             denorm ? mlp->scale : nullptr, mlp->shift);
+  // bias, GELU and the output de-normalisation run in the GEMM epilogues
+  if ((rc = gemm(mlp, n, H, I, mlp->x_bf, I, 0, mlp->w_bf + mlp->oW1, H, 0, mlp->h1, H, 0,
+                 Epilogue{1, mlp->w + mlp->ob1, mlp->h1_bf, nullptr, nullptr, nullptr})))
+    return rc;
+  if ((rc = gemm(mlp, n, H, H, mlp->h1_bf, H, 0, mlp->w_bf + mlp->oW2, H, 0, mlp->h2, H, 0,
+                 Epilogue{1, mlp->w + mlp->ob2, mlp->h2_bf, nullptr, nullptr, nullptr})))
+    return rc;
+  if ((rc = gemm(mlp, n, O, H, mlp->h2_bf, H, 0, mlp->w_bf + mlp->oW3, O, 0, mlp->y, O, 0,
+                 Epilogue{2, mlp->w + mlp->ob3, nullptr, out, denorm ? mlp->scale : nullptr, mlp->shift})))
+    return rc;
   MK(cudaGetLastError(), "forward");
   return 0;
 }
