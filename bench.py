@@ -38,7 +38,7 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_sweep.c
 # DRAM bytes (read + write) of one sweep_kernel launch from an ncu capture, and
 # the sha256 of the kernel source it was taken on; reported as null when the
 # source has changed since.
-NCU_TRAFFIC = {"src_sha256": "1b5d9b09e74de6ac5f7a6af2570a3d3889e5d2f0c57be99367bf1473ebd24edc",
+NCU_TRAFFIC = {"src_sha256": "2b9fa4a9322576864cd3fdba95701cc7a763fb4ee06bc5205a811fc465494cd6",
                "bytes_per_launch": 160249600}  # profiles/sweep_kernel_chain1024.md
 
 

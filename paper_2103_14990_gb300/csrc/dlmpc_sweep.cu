@@ -6,16 +6,20 @@
 // GT threads that synchronise with named barriers.  Every column patch
 // ("item", Sec. III-D) belongs to one group.  A group handles its items in
 // waves: the Phi-step scalars of every row of the wave's patches first (all
-// exchange loads of the wave in flight together), then per item the
-// projection psi = q + N (N^T v) and the Lambda update.
+// exchange loads of the wave in flight together), then per item Psi-comp,
+// Lambda-comp and the residuals.  The first iteration of a step projects the
+// stored Psi and Lambda (project_item: psi = q + N (N^T v)); the later ones run
+// on the compact iterate (project_compact), and the final Psi and Lambda are
+// formed once at the end (expand_compact).
 //
-// Shared memory.  Per group: the Phi-step scalars, v and psi in reduced
-// order, t, per-warp partial sums, and a table of the wave's patch members
-// (exchange offset, |Patch|, s_m, weights, bounds) so the Phi-step issues only
-// the exchange loads.  After the groups: per-CTA counters, then the items'
-// resident data placed by the host: Psi and Lambda, q and, where room remains,
-// N (loaded once per launch by a 1-D bulk TMA copy).  Patches whose N is not
-// resident read it from L2 with batched 16-byte loads.
+// Shared memory.  Per group: the Phi-step scalars, work vectors, per-warp
+// partial sums, a record per patch member and one per patch row (exchange
+// offsets, |Patch|, weights, bounds, 1/s, cost blocks) so the Phi-step issues
+// only the exchange loads.  After the groups: per-CTA counters, then the
+// items' resident data placed by the host: the compact iterate, N (loaded
+// once per launch by a 1-D bulk TMA copy) where room remains, then Psi,
+// Lambda and q.  N of the other patches, and N^T of every patch, are read
+// from L2 in whole 16-byte units.
 //
 // Iteration barrier.  Each CTA adds (1 + not_converged << 32) to one of three
 // rotating 64-bit counters with a release reduction: the low half counts

@@ -109,7 +109,7 @@ def test_learned_start_beats_cold_start_at_same_accuracy():
     assert len(keep) >= 60
     ic, il, sc, sl, uc, ul = W.compare_starts(p, mlp, states[keep])
     assert np.all(sc == 0) and np.all(sl == 0)
-    # measured gain on this shape is about 5% fewer iterations (DESIGN records it)
+    # the measured gain on this shape is about 5% fewer iterations
     assert il.mean() < 0.985 * ic.mean(), (il.mean(), ic.mean())
     assert np.mean(il < ic) > 0.5
     # polished solutions at a tight tolerance agree with the oracle's optimum
