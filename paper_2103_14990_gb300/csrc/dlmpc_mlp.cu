@@ -20,8 +20,9 @@
 namespace {
 
 constexpr int kTile = 64;   // CTA tile (M and N)
-constexpr int kKc = 32;     // K per staged chunk (two m16n8k16 steps)
-constexpr int kLd = 40;     // padded row (bf16) of a shared tile: conflict-free 32-bit fragment loads
+constexpr int kKc = 64;     // K per staged chunk (four m16n8k16 steps)
+constexpr int kLd = 72;     // padded row (bf16) of a shared tile: conflict-free 32-bit fragment loads
+constexpr int kPairs = kTile * kKc / 2 / 128;  // bf16 pairs per thread per operand chunk
 
 __device__ __forceinline__ uint32_t pack2(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
@@ -36,12 +37,12 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
 
 __device__ __forceinline__ float gelu(float x);
 
-// One operand chunk (kTile rows of the M or N side x kKc of K) as 8 pairs of
-// bf16 per thread, read along the source's contiguous dimension.  kcont: the
+// One operand chunk (kTile rows of the M or N side x kKc of K) as kPairs
+// pairs of bf16 per thread, read along the source's contiguous dimension.  kcont: the
 // source is contiguous along K (src[r * ld + k]); otherwise along the row
 // index (src[k * ld + r]).  Out-of-range elements read as zero.
 struct Chunk {
-  uint32_t v[8];
+  uint32_t v[kPairs];
 };
 
 __device__ __forceinline__ uint32_t pair_bits(__nv_bfloat16 lo, __nv_bfloat16 hi) {
@@ -52,12 +53,12 @@ __device__ __forceinline__ void load_chunk(Chunk &c, const __nv_bfloat16 *src, i
                                            int r0, int rmax, int k0, int kmax, int tid) {
   const __nv_bfloat16 zero = __float2bfloat16(0.f);
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < kPairs; ++i) {
     const int e = tid + 128 * i;
     int r, k, r2, k2;
     if (kcont) {
-      r = r0 + (e >> 4);
-      k = k0 + 2 * (e & 15);
+      r = r0 + (e >> 5);
+      k = k0 + 2 * (e & 31);
       r2 = r;
       k2 = k + 1;
     } else {
@@ -81,10 +82,10 @@ __device__ __forceinline__ void load_chunk(Chunk &c, const __nv_bfloat16 *src, i
 // Writes a chunk into the shared tile T[row][k] (row = M or N index).
 __device__ __forceinline__ void store_chunk(const Chunk &c, __nv_bfloat16 (*T)[kLd], bool kcont, int tid) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < kPairs; ++i) {
     const int e = tid + 128 * i;
     if (kcont) {
-      *reinterpret_cast<uint32_t *>(&T[e >> 4][2 * (e & 15)]) = c.v[i];
+      *reinterpret_cast<uint32_t *>(&T[e >> 5][2 * (e & 31)]) = c.v[i];
     } else {
       const int kk = e >> 5, rr = 2 * (e & 31);
       T[rr][kk] = __ushort_as_bfloat16((unsigned short)(c.v[i] & 0xffffu));
@@ -95,7 +96,7 @@ __device__ __forceinline__ void store_chunk(const Chunk &c, __nv_bfloat16 (*T)[k
 
 // C[M x N] (+)= op(A)[M x K] op(B)[K x N]; op(A) = A (A[m*lda+k]) or A^T
 // (A[k*lda+m]); op(B) = B (B[k*ldb+n]) or B^T (B[n*ldb+k]).  BF16 inputs,
-// FP32 accumulate.  128 threads, 4 warps of 32x32; K staged in chunks of 32
+// FP32 accumulate.  128 threads, 4 warps of 32x32; K staged in chunks of 64
 // through shared memory, the next chunk loaded into registers while the
 // current one is multiplied.  Epilogue: epi = 0 stores (or adds) C;
 // epi = 1 adds bias[n], stores C (pre-activation) and act = BF16(GELU(C));
