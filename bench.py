@@ -35,10 +35,10 @@ METRIC = "MPC steps/s & ADMM iters/s, batched+warm-start vs plain at 1e-4 rel; H
 UNIT = "MPC steps/s"
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_sweep.cu")
-# DRAM bytes (read + write) of one sweep_kernel launch from an ncu capture, and
-# the sha256 of the kernel source it was taken on; reported as null when the
-# source has changed since.
-NCU_TRAFFIC = {"src_sha256": "2b9fa4a9322576864cd3fdba95701cc7a763fb4ee06bc5205a811fc465494cd6",
+# DRAM bytes (read + write) of one sweep_kernel launch of a workload from an
+# ncu capture, and the sha256 of the kernel source it was taken on; reported
+# as null for other workloads and when the source has changed since.
+NCU_TRAFFIC = {"workload": "chain1024", "src_sha256": "2b9fa4a9322576864cd3fdba95701cc7a763fb4ee06bc5205a811fc465494cd6",
                "bytes_per_launch": 160249600}  # profiles/sweep_kernel_chain1024.md
 
 
@@ -247,7 +247,8 @@ def run_ours(args):
     # roofline of the sweep kernel: algorithmic bytes / CUDA-event kernel time
     peak, peak_src = measured_peaks()
     achieved = info["iter_bytes"] * tot_iters / kern_s / 1e9
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["src_sha256"] == kernel_sha() else None
+    traffic = (NCU_TRAFFIC["bytes_per_launch"]
+               if NCU_TRAFFIC["src_sha256"] == kernel_sha() and NCU_TRAFFIC["workload"] == args.workload else None)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_src, "kernel": "sweep_kernel",

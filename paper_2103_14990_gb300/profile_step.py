@@ -20,7 +20,7 @@ import numpy as np
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="chain1024", choices=["chain1024", "chain10", "grid64"])
+    ap.add_argument("--workload", default="chain1024", choices=["chain1024", "chain10", "grid64", "batch256"])
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--shape", type=int, default=0)
     ap.add_argument("--residency", type=int, default=-1)
@@ -31,8 +31,10 @@ def main(argv=None) -> int:
     import torch
     import paper_2103_14990_gb300 as pkg
     from paper_2103_14990_gb300 import instances as I
-    p = {"chain1024": I.chain1024, "chain10": I.chain10, "grid64": I.grid64}[a.workload]()
-    s = pkg.Solver([p])
+    probs = I.batch256() if a.workload == "batch256" else \
+        [{"chain1024": I.chain1024, "chain10": I.chain10, "grid64": I.grid64}[a.workload]()]
+    p = probs[0]
+    s = pkg.Solver(probs)
     if a.residency >= 0:
         s.set_option(pkg.OPT_RESIDENCY, a.residency)
     if a.shape > 0:
@@ -45,13 +47,20 @@ def main(argv=None) -> int:
     info = s.info()
     print(json.dumps({k: info[k] for k in ("grid_ctas", "threads_per_cta", "group_threads", "groups_per_cta", "wave",
                                            "smem_bytes", "resident_n_items", "resident_state_items")}))
-    x = torch.tensor(p.x0.astype(np.float32), device="cuda")
-    u = torch.zeros(p.n_sub, p.nu, device="cuda")
+    x = torch.tensor(np.concatenate([q.x0 for q in probs]).astype(np.float32), device="cuda")
+    u = torch.zeros(x.shape[0], p.nu, device="cuda")
     xn = torch.zeros_like(x)
+    if a.shape == 0 and a.residency < 0:
+        s.autotune(x, iters=5)
+        info = s.info()
+        print(json.dumps({"autotuned": {k: info[k] for k in ("group_threads", "groups_per_cta", "wave",
+                                                              "resident_n_items", "iter_bytes")}}))
     for _ in range(a.steps):
         rc, st = s.step(x, u, xn, warm=pkg.WARM_COLD)
         ms = s.timing()[0]
-        print(f"kernel {ms:.4f} ms  {1e3 * ms / a.iters:.2f} us/iteration  status {st[0]['status']}")
+        gbs = s.info()["iter_bytes"] * a.iters / (ms * 1e-3) / 1e9
+        print(f"kernel {ms:.4f} ms  {1e3 * ms / a.iters:.2f} us/iteration  {gbs:.0f} GB/s algorithmic  "
+              f"status {st[0]['status']}")
     if a.trace:
         tr = s.trace().astype(np.int64)
         # stamps: 0 top, 1 Phi-step, 7 pass 1 (+ y), 6 pass 2, 2 first patch done,
