@@ -155,6 +155,17 @@ int dlmpc_setup(const dlmpc_problem *probs, int32_t n_inst, void *stream, dlmpc_
  * if max_c ||Z_j q_c - e_c|| exceeds 1e-9 for some j. Synchronous. */
 int dlmpc_precompute(dlmpc_ctx *ctx);
 
+/* Checkpoint of the one-time precomputation (the paper has no counterpart):
+ * dlmpc_export_operators writes every patch's null-space dimension, N_j, N_j^T
+ * and q_c into the host buffer buf (cap bytes) and returns the blob's size;
+ * with buf NULL or cap too small it only returns the size.
+ * dlmpc_import_operators replaces dlmpc_precompute on a context set up with
+ * the same problem structure (sizes, graphs, T, d; checked by a signature),
+ * from a host blob of `size` bytes; DLMPC_ERR_ARG for a blob of another
+ * structure or a truncated one.  Both synchronous; the caller owns buf. */
+int64_t dlmpc_export_operators(dlmpc_ctx *ctx, void *buf, int64_t cap);
+int dlmpc_import_operators(dlmpc_ctx *ctx, const void *buf, int64_t size);
+
 /* One MPC step for every instance (Alg. 1 body): per-step precompute from
  * x(tau), ADMM to convergence (Alg. 2), u(tau) = slot-0 inputs of Phi x(tau),
  * x(tau+1) = A x(tau) + B u(tau).

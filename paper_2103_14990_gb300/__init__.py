@@ -54,6 +54,7 @@ EXPORTED = [
     "dlmpc_mlp_destroy", "dlmpc_learned_dims", "dlmpc_learned_features", "dlmpc_learned_targets",
     "dlmpc_attach_mlp", "dlmpc_run_variant",
     "dlmpc_factor_patch_noalloc",
+    "dlmpc_export_operators", "dlmpc_import_operators",
 ]
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -107,6 +108,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     vp, fp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)
     lib.dlmpc_setup.argtypes = [ctypes.POINTER(Problem_C), ctypes.c_int32, vp, ctypes.POINTER(vp)]
     lib.dlmpc_precompute.argtypes = [vp]
+    lib.dlmpc_export_operators.argtypes = [vp, vp, ctypes.c_int64]
+    lib.dlmpc_export_operators.restype = ctypes.c_int64
+    lib.dlmpc_import_operators.argtypes = [vp, ctypes.c_void_p, ctypes.c_int64]
     lib.dlmpc_step.argtypes = [vp, vp, vp, vp, ctypes.c_int32, ctypes.POINTER(Stats_C)]
     lib.dlmpc_step_host.argtypes = [vp, fp, fp, fp, ctypes.c_int32, ctypes.POINTER(Stats_C)]
     lib.dlmpc_solve_batch.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -222,6 +226,17 @@ class Solver:
 
     def precompute(self):
         self._check(self.lib.dlmpc_precompute(self._ctx))
+
+    def export_operators(self) -> bytes:
+        """The precomputed operators as a blob (see dlmpc_import_operators)."""
+        n = self._check(int(self.lib.dlmpc_export_operators(self._ctx, None, 0)))
+        buf = ctypes.create_string_buffer(n)
+        m = self._check(int(self.lib.dlmpc_export_operators(self._ctx, buf, n)))
+        return buf.raw[:m]
+
+    def import_operators(self, blob: bytes):
+        """Replaces precompute() on a solver built with precompute=False."""
+        self._check(self.lib.dlmpc_import_operators(self._ctx, blob, len(blob)))
 
     def set_option(self, key: int, value: float):
         self._check(self.lib.dlmpc_set_option(self._ctx, key, float(value)))

@@ -20,6 +20,8 @@
 #include "dlmpc_internal.h"
 #include "../../include/dlmpc.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace dlmpc {
 cudaError_t launch_factor(const FactorParams &p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_repack(const Item *scratch_items, const Item *items, int n_items, const float *src, float *dst,
@@ -110,6 +112,12 @@ struct Instance {
 };
 
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// NVTX range over one entry point (visible to Nsight tools; free otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 }  // namespace
 
@@ -401,6 +409,7 @@ int build_reduced(const Instance &I, int nx, int nu, int j, std::vector<int64_t>
 // ---------------------------------------------------------------------------
 
 extern "C" int dlmpc_setup(const dlmpc_problem *probs, int32_t n_inst, void *stream, dlmpc_ctx **out) {
+  NvtxRange range("dlmpc_setup");
   g_setup_error.clear();
   if (!out || !probs || n_inst < 1) {
     g_setup_error = "dlmpc_setup: null argument or n_inst < 1";
@@ -803,7 +812,137 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
 
 }  // namespace
 
+namespace {
+
+// Packed operator layout from the null-space dimensions: odd row stride kpad,
+// 16-byte aligned items (N then N^T), compact iterates; allocates N (not
+// filled) and the compact iterates and uploads the items.
+int operator_layout(dlmpc_ctx *ctx, const std::vector<int32_t> &nul) {
+  cudaStream_t s = ctx->stream;
+  int64_t noff = 0;
+  ctx->max_kpad = 1;
+  for (int g = 0; g < ctx->n_sub; ++g) {
+    Item &it = ctx->items[g];
+    it.k = nul[g];
+    // row stride: multiple of 4 floats (16-byte vector loads) with an odd
+    // number of 16-byte units, so consecutive rows hit distinct bank groups
+    it.kpad = (int)round_up(std::max(it.k, 1), 4);
+    if ((it.kpad / 4) % 2 == 0) it.kpad += 4;
+    it.n_off = noff;
+    noff += round_up((int64_t)n_floats(it), 4);
+    ctx->max_kpad = std::max(ctx->max_kpad, it.kpad);
+    ctx->max_dred_pad = std::max(ctx->max_dred_pad, it.dred_pad);
+  }
+  ctx->n_floats = noff;
+  int64_t cpoff = 0;
+  for (Item &it : ctx->items) {
+    it.cp_off = cpoff;
+    it.cp_sm = -1;
+    cpoff += cp_floats(it, ctx->nx);
+  }
+  CK(ctx->d_cp.alloc(std::max<int64_t>(cpoff, 4)), "alloc compact iterates");
+  CK(upload(ctx->d_items, ctx->items, s), "upload items");
+  CK(ctx->d_N.alloc(noff), "alloc N");
+  return 0;
+}
+
+// Default launch plan (the first shape that fits the shared-memory budget).
+int finish_precompute(dlmpc_ctx *ctx) {
+  static const int kShapes[][3] = {{128, 8, 1}, {128, 6, 1}, {128, 4, 2}, {128, 4, 1}, {128, 2, 1},
+                                   {256, 2, 1}, {128, 1, 1}, {256, 1, 1}, {64, 1, 1}};
+  int rc = DLMPC_ERR_ARG;
+  for (const auto &sh : kShapes) {
+    rc = plan_sweep(ctx, sh[0], sh[1], sh[2]);
+    if (rc == 0) break;
+  }
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(ctx->stream), "precompute");
+  ctx->precomputed = true;
+  return DLMPC_OK;
+}
+
+// Structure signature of a context's operators: nx, items, and per item the
+// sizes that fix the operator layout.
+uint64_t operator_signature(const dlmpc_ctx *ctx) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&h](uint64_t v) {
+    h ^= v;
+    h *= 1099511628211ull;
+  };
+  mix((uint64_t)ctx->nx);
+  mix((uint64_t)ctx->nu);
+  mix((uint64_t)ctx->n_sub);
+  for (const Item &it : ctx->items) {
+    mix((uint64_t)it.r_sub);
+    mix((uint64_t)it.n_mem);
+    mix((uint64_t)it.dred);
+    mix((uint64_t)it.self_pos);
+  }
+  return h;
+}
+
+constexpr uint64_t kOperatorMagic = 0x3150504f434d4c44ull;  // "DLMCOPP1"
+
+}  // namespace
+
+// Blob: magic, signature, n_items, n_floats, q_floats (int64 each), k per
+// item (int32), N and N^T (n_floats FP32), q (q_floats FP32).
+extern "C" int64_t dlmpc_export_operators(dlmpc_ctx *ctx, void *buf, int64_t cap) {
+  if (!ctx) return DLMPC_ERR_ARG;
+  if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
+  const int64_t need = 5 * 8 + (int64_t)ctx->n_sub * 4 + (ctx->n_floats + ctx->q_floats) * 4;
+  if (!buf || cap < need) return need;
+  auto *p = static_cast<unsigned char *>(buf);
+  const int64_t head[5] = {(int64_t)kOperatorMagic, (int64_t)operator_signature(ctx), ctx->n_sub, ctx->n_floats,
+                           ctx->q_floats};
+  std::memcpy(p, head, sizeof head);
+  p += sizeof head;
+  for (const Item &it : ctx->items) {
+    const int32_t k = it.k;
+    std::memcpy(p, &k, 4);
+    p += 4;
+  }
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync(p, ctx->d_N.p, ctx->n_floats * 4, cudaMemcpyDeviceToHost, s), "D2H N");
+  p += ctx->n_floats * 4;
+  CK(cudaMemcpyAsync(p, ctx->d_q.p, ctx->q_floats * 4, cudaMemcpyDeviceToHost, s), "D2H q");
+  CK(cudaStreamSynchronize(s), "export");
+  return need;
+}
+
+extern "C" int dlmpc_import_operators(dlmpc_ctx *ctx, const void *buf, int64_t size) {
+  NvtxRange range("dlmpc_import_operators");
+  if (!ctx || !buf || size < 40) return ctx ? ctx->fail(DLMPC_ERR_ARG, "no operator blob") : DLMPC_ERR_ARG;
+  const auto *p = static_cast<const unsigned char *>(buf);
+  int64_t head[5];
+  std::memcpy(head, p, sizeof head);
+  p += sizeof head;
+  if (head[0] != (int64_t)kOperatorMagic) return ctx->fail(DLMPC_ERR_ARG, "not an operator blob");
+  if (head[1] != (int64_t)operator_signature(ctx) || head[2] != ctx->n_sub)
+    return ctx->fail(DLMPC_ERR_ARG, "operator blob of another problem structure");
+  if (size != 40 + head[2] * 4 + (head[3] + head[4]) * 4) return ctx->fail(DLMPC_ERR_ARG, "truncated operator blob");
+  int rc = upload_static(ctx);
+  if (rc) return rc;
+  std::vector<int32_t> nul(ctx->n_sub);
+  std::memcpy(nul.data(), p, (size_t)ctx->n_sub * 4);
+  p += (size_t)ctx->n_sub * 4;
+  for (int g = 0; g < ctx->n_sub; ++g)
+    if (nul[g] < 0 || nul[g] > ctx->kub[g]) return ctx->fail(DLMPC_ERR_ARG, "operator blob: bad null-space size");
+  rc = operator_layout(ctx, nul);
+  if (rc) return rc;
+  if (ctx->n_floats != head[3] || ctx->q_floats != head[4])
+    return ctx->fail(DLMPC_ERR_ARG, "operator blob: layout mismatch");
+  cudaStream_t s = ctx->stream;
+  CK(ctx->d_q.alloc(ctx->q_floats), "alloc q");
+  CK(cudaMemcpyAsync(ctx->d_N.p, p, ctx->n_floats * 4, cudaMemcpyHostToDevice, s), "H2D N");
+  p += ctx->n_floats * 4;
+  CK(cudaMemcpyAsync(ctx->d_q.p, p, ctx->q_floats * 4, cudaMemcpyHostToDevice, s), "H2D q");
+  CK(cudaStreamSynchronize(s), "import");
+  return finish_precompute(ctx);
+}
+
 extern "C" int dlmpc_precompute(dlmpc_ctx *ctx) {
+  NvtxRange range("dlmpc_precompute");
   if (!ctx) return DLMPC_ERR_ARG;
   const int nx = ctx->nx;
   cudaStream_t s = ctx->stream;
@@ -879,45 +1018,11 @@ extern "C" int dlmpc_precompute(dlmpc_ctx *ctx) {
     if (nul[g] > ctx->kub[g]) return ctx->fail(DLMPC_ERR_ARG, "null-space dimension above its structural bound");
     if (nul[g] > 1000) return ctx->fail(DLMPC_ERR_ARG, "null-space dimension above 1000");
   }
-  // packed layout: odd stride kpad, 16-byte aligned items
-  int64_t noff = 0;
-  ctx->max_kpad = 1;
-  for (int g = 0; g < ctx->n_sub; ++g) {
-    Item &it = ctx->items[g];
-    it.k = nul[g];
-    // row stride: multiple of 4 floats (16-byte vector loads) with an odd
-    // number of 16-byte units, so consecutive rows hit distinct bank groups
-    it.kpad = (int)round_up(std::max(it.k, 1), 4);
-    if ((it.kpad / 4) % 2 == 0) it.kpad += 4;
-    it.n_off = noff;
-    noff += round_up((int64_t)n_floats(it), 4);
-    ctx->max_kpad = std::max(ctx->max_kpad, it.kpad);
-    ctx->max_dred_pad = std::max(ctx->max_dred_pad, it.dred_pad);
-  }
-  ctx->n_floats = noff;
-  int64_t cpoff = 0;
-  for (Item &it : ctx->items) {
-    it.cp_off = cpoff;
-    it.cp_sm = -1;
-    cpoff += cp_floats(it, nx);
-  }
-  CK(ctx->d_cp.alloc(std::max<int64_t>(cpoff, 4)), "alloc compact iterates");
-  CK(upload(ctx->d_items, ctx->items, s), "upload items");
-  CK(ctx->d_N.alloc(noff), "alloc N");
+  rc = operator_layout(ctx, nul);
+  if (rc) return rc;
   CK(launch_repack(d_scr.p, ctx->d_items.p, ctx->n_sub, d_Nscr.p, ctx->d_N.p, s), "repack_kernel");
   CK(cudaStreamSynchronize(s), "repack");
-  // default launch shape: the first that fits the shared-memory budget
-  static const int kShapes[][3] = {{128, 8, 1}, {128, 6, 1}, {128, 4, 2}, {128, 4, 1}, {128, 2, 1},
-                                   {256, 2, 1}, {128, 1, 1}, {256, 1, 1}, {64, 1, 1}};
-  rc = DLMPC_ERR_ARG;
-  for (const auto &sh : kShapes) {
-    rc = plan_sweep(ctx, sh[0], sh[1], sh[2]);
-    if (rc == 0) break;
-  }
-  if (rc) return rc;
-  CK(cudaStreamSynchronize(s), "precompute");
-  ctx->precomputed = true;
-  return DLMPC_OK;
+  return finish_precompute(ctx);
 }
 
 namespace {
@@ -1099,6 +1204,7 @@ extern "C" int dlmpc_get_timing(dlmpc_ctx *ctx, float *ms);
 namespace {
 
 int run_step(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_dev, int warm, dlmpc_stats *stats) {
+  NvtxRange range(warm == DLMPC_WARM_LEARNED ? "dlmpc_step (learned start)" : "dlmpc_step");
   if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
   if (warm != DLMPC_WARM_COLD && warm != DLMPC_WARM_PREVIOUS && warm != DLMPC_WARM_LEARNED)
     return ctx->fail(DLMPC_ERR_ARG, "unsupported warm-start mode");
@@ -1222,6 +1328,7 @@ extern "C" int dlmpc_mlp_forward(dlmpc_mlp *mlp, const float *x_dev, int32_t n, 
 extern "C" const char *dlmpc_mlp_last_error(dlmpc_mlp *mlp);
 extern "C" int dlmpc_autotune(dlmpc_ctx *ctx, const float *x_dev, int32_t iters, dlmpc_tune_entry *entries,
                               int32_t cap) {
+  NvtxRange range("dlmpc_autotune");
   if (!ctx || !x_dev) return DLMPC_ERR_ARG;
   if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
   const TuneSig sig = signature(ctx);

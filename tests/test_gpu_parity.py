@@ -407,3 +407,49 @@ def test_block_cost_validation(torch):
     with pytest.raises(pkg.DlmpcError):
         s.run_variant(0, x, 2)                            # the paper variants take diagonal weights
     s.close()
+
+
+def test_steps_are_deterministic(torch):
+    """No atomics sit in value paths: the same step twice gives the same bits
+    (state, u, x(t+1), statistics)."""
+    import paper_2103_14990_gb300 as pkg
+    p = SMALL["grid5x5_T6_d2_box"]()
+    outs = []
+    for _ in range(2):
+        s = gpu_solver([p], torch)
+        x = torch.tensor(p.x0.astype(np.float32), device="cuda")
+        u = torch.zeros(p.n_sub, 1, device="cuda")
+        xn = torch.zeros_like(x)
+        rc, st = s.step(x, u, xn, warm=pkg.WARM_COLD)
+        rc2, st2 = s.step(xn.clone(), u, xn, warm=pkg.WARM_PREVIOUS)
+        _, psi, lam = s.get_state()
+        outs.append((psi.cpu().numpy(), lam.cpu().numpy(), u.cpu().numpy(), xn.cpu().numpy(), st, st2))
+        s.close()
+    a, b = outs
+    for i in range(4):
+        assert np.array_equal(a[i], b[i])
+    assert a[4] == b[4] and a[5] == b[5]
+
+
+def test_operator_checkpoint_round_trip(torch):
+    """Operators exported after precompute and imported into a fresh context
+    (no factorisation) give the same iterates bit for bit; a blob of another
+    problem structure is refused."""
+    import paper_2103_14990_gb300 as pkg
+    p = SMALL["grid5x5_T6_d2_box"]()
+    a = gpu_solver([p], torch)
+    blob = a.export_operators()
+    b = pkg.Solver([p], precompute=False)
+    b.import_operators(blob)
+    ra = run_fixed(a, torch, p.x0, 25)
+    rb = run_fixed(b, torch, p.x0, 25)
+    for x, y in zip(ra[2:], rb[2:]):
+        assert np.array_equal(x, y)
+    other = pkg.Solver([SMALL["chain16_T10_d3_box"]()], precompute=False)
+    with pytest.raises(pkg.DlmpcError):
+        other.import_operators(blob)
+    with pytest.raises(pkg.DlmpcError):
+        b2 = pkg.Solver([p], precompute=False)
+        b2.import_operators(blob[:-8])
+    for s in (a, b, other):
+        s.close()
