@@ -13,6 +13,10 @@ Pinned parts (see tests/test_oracle_pins.py):
   * box_qp, phi_step_block (full Q_i, R_i blocks) - against scipy's bounded
                     minimiser, the diagonal closed form, the Riccati gain with
                     full blocks and the centralised boxed QP with full blocks;
+  * poly_qp, slot_constraints (coupled per-slot rows) - against scipy's SLSQP,
+                    box_qp when the rows are a box, the closed-form projection
+                    onto one half-space, a degenerate vertex, and the
+                    centralised QP with coupled rows (KKT at the ADMM solution);
   * psi projector - Z psi = e exactly, idempotent symmetric projector, min-norm offset
                     against lstsq, residual orthogonal to the null space;
   * admm / mpc    - converged trajectory against the centralised
@@ -315,6 +319,67 @@ def box_qp(H: np.ndarray, c: np.ndarray, lo: np.ndarray, hi: np.ndarray) -> np.n
     raise RuntimeError("box_qp: no KKT point (H not positive definite?)")
 
 
+def poly_qp(H: np.ndarray, c: np.ndarray, A: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """argmin 1/2 z^T H z - c^T z  s.t.  A z <= b, H symmetric positive
+    definite, n <= 4 unknowns and a few rows.  Active-set enumeration of the
+    KKT conditions: for every set S of at most n rows whose A_S has full row
+    rank, the stationarity and the active rows give
+        [H  A_S^T] [z ]   [c  ]
+        [A_S  0  ] [mu] = [b_S],
+    and S is accepted when z satisfies every row and mu >= 0.  A strictly
+    convex QP has one optimum; its active rows contain a linearly independent
+    subset carrying non-negative multipliers (Caratheodory on the normal cone),
+    so the enumeration meets it."""
+    n, m = len(c), len(b)
+    tol = 1e-12 * (1.0 + np.max(np.abs(c)) + np.max(np.abs(H)) + (np.max(np.abs(b)) if m else 0.0))
+    for k in range(0, min(n, m) + 1):
+        for S in itertools.combinations(range(m), k):
+            S = list(S)
+            As = A[S]
+            if k and np.linalg.matrix_rank(As, tol=1e-10) < k:
+                continue
+            K = np.block([[H, As.T], [As, np.zeros((k, k))]]) if k else H
+            sol = np.linalg.solve(K, np.concatenate([c, b[S]]) if k else c)
+            z, mu = sol[:n], sol[n:]
+            if m and np.any(A @ z > b + tol):
+                continue
+            if np.any(mu < -tol):
+                continue
+            return z
+    raise RuntimeError("poly_qp: no KKT point (infeasible rows or H not positive definite?)")
+
+
+def slot_constraints(prob, i: int, kind: str, t: int):
+    """Rows (A, b) of A z <= b on the slot vector z of subsystem i: kind "x"
+    for the state slot t, "u" for the input slot t.  The boxes (finite bounds
+    only) come first as -z_a <= -lo_a and z_a <= hi_a, then the coupled rows
+    Gx[i] (states, t >= 1) or Gu[i] (inputs).  The slot-0 state has none: it is
+    pinned by Z_AB Psi = I."""
+    n = prob.nx if kind == "x" else prob.nu
+    if kind == "x":
+        if t == 0:
+            return np.zeros((0, n)), np.zeros(0)
+        lo, hi = (prob.x_lo[i], prob.x_hi[i]) if prob.x_lo is not None else (None, None)
+        G, g = (prob.Gx[i], prob.gx[i]) if prob.Gx is not None else (None, None)
+    else:
+        lo, hi = (prob.u_lo[i], prob.u_hi[i]) if prob.u_lo is not None else (None, None)
+        G, g = (prob.Gu[i], prob.gu[i]) if prob.Gu is not None else (None, None)
+    rows, rhs = [], []
+    if lo is not None:
+        for a in range(n):
+            if np.isfinite(lo[a]):
+                e = np.zeros(n); e[a] = -1.0
+                rows.append(e); rhs.append(-lo[a])
+        for a in range(n):
+            if np.isfinite(hi[a]):
+                e = np.zeros(n); e[a] = 1.0
+                rows.append(e); rhs.append(hi[a])
+    if G is not None:
+        for k in range(G.shape[0]):
+            rows.append(np.asarray(G[k], float)); rhs.append(float(g[k]))
+    return (np.array(rows).reshape(-1, n), np.array(rhs))
+
+
 def phi_step_block(lay: Layout, Psi: np.ndarray, Lam: np.ndarray, x0: np.ndarray, rho: float):
     """Phi-comp with full cost blocks Q_i, R_i (Sec. II-A with non-diagonal
     Q_t, R_t): the rows of subsystem i at one time slot (its nx state rows, or
@@ -322,7 +387,9 @@ def phi_step_block(lay: Layout, Psi: np.ndarray, Lam: np.ndarray, x0: np.ndarray
     s = ||x_hat_i||^2 and z = Phi x_hat, the slot's rows solve
         min z^T Q_i z + rho/(2 s) ||z - w||^2  s.t.  lo <= z <= hi,
     a box-QP with H = 2 Q_i + (rho/s) I and c = (rho/s) w (box_qp); each row is
-    then v + ((z - w)/s) x_hat.  s = 0 gives phi = v.  Returns (Phi, z)."""
+    then v + ((z - w)/s) x_hat.  s = 0 gives phi = v.  With coupled
+    constraints (Gx / Gu) the slot QP takes them beside the box
+    (slot_constraints, poly_qp).  Returns (Phi, z)."""
     prob = lay.prob
     nx, nu, T = prob.nx, prob.nu, prob.T
     xf = x0.reshape(-1)
@@ -332,18 +399,24 @@ def phi_step_block(lay: Layout, Psi: np.ndarray, Lam: np.ndarray, x0: np.ndarray
     s = np.bincount(lay.rows, weights=xe * xe, minlength=lay.n_rows)
     Qb = prob.Q_blk if prob.Q_blk is not None else np.array([np.diag(q) for q in prob.q])
     Rb = prob.R_blk if prob.R_blk is not None else np.array([np.diag(r) for r in prob.r])
+    coupled = prob.Gx is not None or prob.Gu is not None
     z = w.copy()
     alpha = np.zeros(lay.n_rows)
     for i in range(prob.n_sub):
-        groups = [([global_row(prob, i, t * nx + a) for a in range(nx)], Qb[i]) for t in range(T)]
-        groups += [([global_row(prob, i, nx * T + t * nu + b) for b in range(nu)], Rb[i]) for t in range(T - 1)]
-        for rows, C in groups:
+        groups = [([global_row(prob, i, t * nx + a) for a in range(nx)], Qb[i], "x", t) for t in range(T)]
+        groups += [([global_row(prob, i, nx * T + t * nu + b) for b in range(nu)], Rb[i], "u", t)
+                   for t in range(T - 1)]
+        for rows, C, kind, t in groups:
             rows = np.asarray(rows)
             si = s[rows[0]]
             if si == 0.0:
                 continue
             H = 2.0 * C + (rho / si) * np.eye(len(rows))
-            zz = box_qp(H, (rho / si) * w[rows], lay.lo[rows], lay.hi[rows])
+            if coupled:
+                Ac, bc = slot_constraints(prob, i, kind, t)
+                zz = poly_qp(H, (rho / si) * w[rows], Ac, bc)
+            else:
+                zz = box_qp(H, (rho / si) * w[rows], lay.lo[rows], lay.hi[rows])
             z[rows] = zz
             alpha[rows] = (zz - w[rows]) / si
     Phi = V + alpha[lay.rows] * xe
@@ -408,7 +481,8 @@ def admm(lay: Layout, blocks: List[ColumnBlock], x0: np.ndarray, *,
     it = 0
     r_max = s_max = np.inf
     Phi = z = None
-    block = prob.Q_blk is not None or prob.R_blk is not None
+    block = (prob.Q_blk is not None or prob.R_blk is not None
+             or prob.Gx is not None or prob.Gu is not None)
     for it in range(1, n_it + 1):
         Phi, z = (phi_step_block if block else phi_step)(lay, Psi, Lam, x0, rho)
         Psi_new = psi_step(lay, blocks, Phi + Lam)

@@ -63,6 +63,13 @@ class Problem:
     grid_shape: Optional[tuple] = None
     Q_blk: Optional[np.ndarray] = None  # f64 [n_sub, nx, nx] full SPD Q_i (replaces q), or None
     R_blk: Optional[np.ndarray] = None  # f64 [n_sub, nu, nu] full SPD R_i (replaces r), or None
+    # Coupled constraints of one subsystem at one time slot, beside the boxes:
+    # Gx[i] x_t <= gx[i] for the state slots t = 1..T-1, Gu[i] u_t <= gu[i] for
+    # every input slot.  Gx f64 [n_sub, n_cx, nx], gx f64 [n_sub, n_cx]; None = none.
+    Gx: Optional[np.ndarray] = None
+    gx: Optional[np.ndarray] = None
+    Gu: Optional[np.ndarray] = None
+    gu: Optional[np.ndarray] = None
 
     @property
     def r_sub(self) -> int:
@@ -205,6 +212,33 @@ def with_block_costs(p: Problem, seed: int, coupling: float = 0.5) -> Problem:
                               r=np.array([np.diag(b) for b in R]),
                               name=(p.name + "_blockQR") if p.name else "")
     return out
+
+
+def with_coupled_constraints(p: Problem, seed: int, n_cx: int = 2, n_cu: int = 0,
+                             g_range: tuple = (0.4, 0.8)) -> Problem:
+    """A copy of p with coupled per-slot constraints: n_cx half-spaces
+    a^T x_t <= g on each subsystem's state and n_cu on its input, a a unit
+    vector of random direction, g ~ U[g_range] (so 0 is strictly feasible).
+    Draw order (numpy PCG64 `default_rng(seed)`): per subsystem, the n_cx state
+    rows (a then g), then the n_cu input rows.  Full cost blocks are added when
+    p has none (the coupled Phi-step runs on the slot QP)."""
+    rng = np.random.default_rng(seed)
+    nx, nu = p.nx, p.nu
+    Gx = np.zeros((p.n_sub, n_cx, nx)); gx = np.zeros((p.n_sub, n_cx))
+    Gu = np.zeros((p.n_sub, n_cu, nu)); gu = np.zeros((p.n_sub, n_cu))
+    for i in range(p.n_sub):
+        for k in range(n_cx):
+            a = rng.normal(size=nx)
+            Gx[i, k] = a / np.linalg.norm(a)
+            gx[i, k] = rng.uniform(*g_range)
+        for k in range(n_cu):
+            a = rng.normal(size=nu)
+            Gu[i, k] = a / np.linalg.norm(a)
+            gu[i, k] = rng.uniform(*g_range)
+    base = p if p.Q_blk is not None else with_block_costs(p, seed + 1)
+    return dataclasses.replace(base, Gx=Gx if n_cx else None, gx=gx if n_cx else None,
+                               Gu=Gu if n_cu else None, gu=gu if n_cu else None,
+                               name=(base.name + "_coupled") if base.name else "")
 
 
 # --- the five workloads -------------------------------------------------------

@@ -499,3 +499,213 @@ def test_block_phi_step_matches_slsqp_on_the_slot_problem(seed):
         got = np.concatenate([Phi[e] for e in sel])
         assert np.allclose(got, res.x, atol=1e-6), (seed, rows)
         assert f(got) <= res.fun + 1e-9
+
+
+# --------------------------------------------------------------------------
+# Coupled per-slot constraints: the slot QP over a polytope (poly_qp)
+# --------------------------------------------------------------------------
+
+def _spd(rng, n):
+    M = rng.normal(size=(n, n))
+    return M @ M.T + 0.3 * np.eye(n)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_poly_qp_matches_slsqp(seed):
+    """Random strictly convex QPs with a few half-spaces (0 strictly feasible)
+    against scipy's SLSQP; the linear term is scaled so that some rows bind."""
+    rng = np.random.default_rng(100 + seed)
+    n = 1 + seed % 4
+    m = 2 + seed % 5
+    H = _spd(rng, n)
+    c = 4.0 * rng.normal(size=n)
+    A = rng.normal(size=(m, n))
+    b = rng.uniform(0.2, 1.0, m)
+    z = O.poly_qp(H, c, A, b)
+    f = lambda v: 0.5 * v @ H @ v - c @ v
+    res = scipy.optimize.minimize(f, np.zeros(n), jac=lambda v: H @ v - c, method="SLSQP",
+                                  constraints=[{"type": "ineq", "fun": lambda v: b - A @ v,
+                                                "jac": lambda v: -A}],
+                                  options={"ftol": 1e-13, "maxiter": 1000})
+    # SLSQP may stop on its line search this close to the optimum: its point
+    # must still be feasible, and the enumeration's point no worse
+    assert np.all(A @ res.x <= b + 1e-8)
+    assert np.all(A @ z <= b + 1e-10)
+    assert np.allclose(z, res.x, atol=1e-5)
+    assert f(z) <= f(res.x) + 1e-10
+    z_unc = np.linalg.solve(H, c)
+    if np.any(A @ z_unc > b):                     # the unconstrained optimum is cut off
+        assert np.max(A @ z - b) > -1e-9         # so some row binds
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_poly_qp_with_box_rows_is_box_qp(seed):
+    rng = np.random.default_rng(200 + seed)
+    n = 1 + seed % 4
+    H = _spd(rng, n)
+    c = 3.0 * rng.normal(size=n)
+    lo, hi = -rng.uniform(0.1, 0.8, n), rng.uniform(0.1, 0.8, n)
+    A = np.vstack([-np.eye(n), np.eye(n)])
+    b = np.concatenate([-lo, hi])
+    assert np.allclose(O.poly_qp(H, c, A, b), O.box_qp(H, c, lo, hi), atol=1e-12)
+
+
+def test_poly_qp_single_half_space_closed_form():
+    """One row a^T z <= g: the optimum is the H-metric projection of the
+    unconstrained minimiser z_u onto the half-space,
+    z = z_u - H^{-1} a (a^T z_u - g) / (a^T H^{-1} a) when a^T z_u > g."""
+    rng = np.random.default_rng(7)
+    for n in (1, 2, 3, 4):
+        H = _spd(rng, n)
+        a = rng.normal(size=n)
+        z_u = rng.normal(size=n)
+        g = a @ z_u - 0.5                         # violated by 0.5
+        Hia = np.linalg.solve(H, a)
+        z_ref = z_u - Hia * (a @ z_u - g) / (a @ Hia)
+        z = O.poly_qp(H, H @ z_u, a[None, :], np.array([g]))
+        assert np.allclose(z, z_ref, atol=1e-12)
+        # inactive: the unconstrained minimiser itself
+        z2 = O.poly_qp(H, H @ z_u, a[None, :], np.array([a @ z_u + 0.5]))
+        assert np.allclose(z2, z_u, atol=1e-12)
+
+
+def test_poly_qp_degenerate_vertex():
+    """Three rows through the origin of the plane (z1 <= 0, z2 <= 0,
+    z1 + z2 <= 0) and a pull towards (5, 5): the optimum is the vertex 0,
+    where the three active rows are linearly dependent."""
+    A = np.array([[1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
+    z = O.poly_qp(np.eye(2), np.array([5.0, 5.0]), A, np.zeros(3))
+    assert np.allclose(z, 0.0, atol=1e-12)
+    # a pull along (1, -1) slides along z1 + z2 = 0 only if z2 <= 0 allows it
+    z = O.poly_qp(np.eye(2), np.array([2.0, -1.0]), A, np.zeros(3))
+    assert np.allclose(z, [0.0, -1.0], atol=1e-12)
+
+
+def _slot_rows(p, i, kind, t):
+    if kind == "x":
+        return [O.global_row(p, i, t * p.nx + a) for a in range(p.nx)]
+    return [O.global_row(p, i, p.nx * p.T + t * p.nu + b) for b in range(p.nu)]
+
+
+def test_slot_constraints_rows():
+    p = I.with_coupled_constraints(I.make_instance(4, 4, 1, seed=2, boxes=True, x0_dist="uniform"),
+                                   seed=5, n_cx=2, n_cu=1)
+    A, b = O.slot_constraints(p, 1, "x", 0)
+    assert A.shape == (0, p.nx)                   # slot 0 is pinned, not constrained
+    A, b = O.slot_constraints(p, 1, "x", 2)
+    assert A.shape == (2 * p.nx + 2, p.nx)
+    assert np.allclose(A[:p.nx], -np.eye(p.nx)) and np.allclose(b[:p.nx], -p.x_lo[1])
+    assert np.allclose(A[p.nx:2 * p.nx], np.eye(p.nx)) and np.allclose(b[p.nx:2 * p.nx], p.x_hi[1])
+    assert np.allclose(A[2 * p.nx:], p.Gx[1]) and np.allclose(b[2 * p.nx:], p.gx[1])
+    A, b = O.slot_constraints(p, 3, "u", 0)
+    assert A.shape == (2 * p.nu + 1, p.nu)
+    assert np.allclose(A[-1], p.Gu[3]) and np.isclose(b[-1], p.gu[3, 0])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_coupled_phi_step_matches_slsqp_on_the_slot_problem(seed):
+    """One state slot and one input slot of one subsystem with coupled rows,
+    solved directly in the Phi entries of the slot's rows by SLSQP:
+    min (Phi_s xh)^T C (Phi_s xh) + rho/2 ||Phi_s - V_s||^2 s.t. the box and the
+    coupled rows on Phi_s xh."""
+    p = I.with_coupled_constraints(
+        I.make_instance(5, 4, 1, seed=seed, boxes=True, x0_dist="uniform", x_bound=0.8, u_bound=0.5),
+        seed=seed + 30, n_cx=2, n_cu=1, g_range=(0.05, 0.3))
+    rng = np.random.default_rng(seed)
+    lay = O.Layout(p)
+    Psi, Lam = rng.normal(size=lay.nnz) * 0.7, rng.normal(size=lay.nnz) * 0.3
+    Phi, z_all = O.phi_step_block(lay, Psi, Lam, p.x0, p.rho)
+    V = Psi - Lam
+    xf = p.x0.reshape(-1)
+    i = 2
+    binds = 0
+    for kind, t, C in [("x", 1, p.Q_blk[i]), ("u", 0, p.R_blk[i])]:
+        rows = _slot_rows(p, i, kind, t)
+        Ac, bc = O.slot_constraints(p, i, kind, t)
+        sel = [np.nonzero(lay.rows == r)[0] for r in rows]
+        xh = [xf[lay.cols[e]] for e in sel]
+        v = [V[e] for e in sel]
+        sizes = [len(e) for e in sel]
+
+        def unpack(theta):
+            out, o = [], 0
+            for k in sizes:
+                out.append(theta[o:o + k]); o += k
+            return out
+
+        def zof(theta):
+            ph = unpack(theta)
+            return np.array([ph[a] @ xh[a] for a in range(len(rows))])
+
+        def f(theta):
+            ph, z = unpack(theta), zof(theta)
+            return z @ C @ z + 0.5 * p.rho * sum(np.sum((ph[a] - v[a]) ** 2) for a in range(len(rows)))
+
+        res = scipy.optimize.minimize(f, np.concatenate(v), method="SLSQP",
+                                      constraints=[{"type": "ineq", "fun": lambda th: bc - Ac @ zof(th)}],
+                                      options={"ftol": 1e-15, "maxiter": 3000})
+        assert res.success
+        got = np.concatenate([Phi[e] for e in sel])
+        assert np.allclose(got, res.x, atol=1e-6), (seed, kind)
+        assert f(got) <= res.fun + 1e-9
+        binds += int(np.max(Ac @ z_all[rows] - bc) > -1e-9)
+    assert binds >= 1, "some slot row must bind"
+
+
+def test_coupled_admm_matches_centralised_qp():
+    """Full blocks, boxes and coupled state rows: the converged trajectory
+    solves the centralised QP min y^T W y over the locality-constrained affine
+    set with every slot's rows A_s y_s <= b_s; checked by the KKT conditions of
+    that QP at the ADMM solution (feasibility, stationarity with multipliers
+    on the active rows only, their signs), with a coupled row active."""
+    base = I.make_instance(4, 4, 1, seed=3, boxes=True, x0_dist="uniform", x_bound=1.0, u_bound=0.5)
+    base.x0 = 0.3 * base.x0
+    p = I.with_coupled_constraints(base, seed=8, n_cx=2, n_cu=0, g_range=(0.1, 0.3))
+    lay, y0, G = _centralised_affine(p, p.x0)
+    U, S, _ = np.linalg.svd(G, full_matrices=False)
+    Bm = U[:, S > 1e-10 * S[0]]
+    W = np.zeros((lay.n_rows, lay.n_rows))
+    rows_all, rhs_all, coupled = [], [], []
+    for i in range(p.n_sub):
+        for kind, slots, C in [("x", range(p.T), p.Q_blk[i]), ("u", range(p.T - 1), p.R_blk[i])]:
+            for t in slots:
+                rr = _slot_rows(p, i, kind, t)
+                W[np.ix_(rr, rr)] = C
+                Ac, bc = O.slot_constraints(p, i, kind, t)
+                nbox = Ac.shape[0] - (p.Gx.shape[1] if (kind == "x" and t >= 1) else 0)
+                for k in range(Ac.shape[0]):
+                    row = np.zeros(lay.n_rows); row[rr] = Ac[k]
+                    rows_all.append(row); rhs_all.append(bc[k]); coupled.append(k >= nbox)
+    Arow, brow, coupled = np.array(rows_all), np.array(rhs_all), np.array(coupled)
+    o = O.Oracle(p)
+    res = O.admm(o.lay, o.blocks, p.x0, max_iter=5000, eps_p=1e-10, eps_d=1e-10)
+    assert res.status == O.STATUS_CONVERGED
+    y = o.lay.trajectory(res.Phi, p.x0)
+    assert np.allclose(y0 + Bm @ (Bm.T @ (y - y0)), y, atol=1e-8)
+    slack = Arow @ y - brow
+    assert np.all(slack <= 1e-8)
+    act = slack >= -1e-7
+    assert np.any(act & coupled), "a coupled row must be active"
+    grad = 2 * Bm.T @ (W @ y)
+    Cm = (Arow[act] @ Bm).T
+    mu = np.linalg.lstsq(Cm, -grad, rcond=None)[0]
+    assert np.allclose(Cm @ mu, -grad, atol=1e-6)
+    assert np.all(mu >= -1e-6)
+
+
+def test_planted_coupled_sign_flip_is_caught(monkeypatch):
+    """A slot QP that reads the coupled rows with the wrong sign fails the
+    centralised check above."""
+    real = O.slot_constraints
+
+    def flipped(prob, i, kind, t):
+        A, b = real(prob, i, kind, t)
+        n = prob.nx if kind == "x" else prob.nu
+        if kind == "x" and t >= 1 and prob.Gx is not None:
+            k = prob.Gx.shape[1]
+            A = A.copy(); A[-k:] *= -1.0
+        return A, b
+
+    monkeypatch.setattr(O, "slot_constraints", flipped)
+    with pytest.raises(AssertionError):
+        test_coupled_admm_matches_centralised_qp()
