@@ -81,7 +81,25 @@ typedef struct {
    * subsystem and time slot, the box-QP of the slot's nx (or nu) rows exactly. */
   const double *Q_blk;
   const double *R_blk;
+  /* Coupled constraints of one subsystem at one time slot, beside the boxes
+   * (Sec. II-A: the Phi-comp then has a piecewise-affine explicit solution,
+   * precomputed at every MPC step from x(tau) as in Alg. 1):
+   *   Gx[i] x_t <= gx[i]  on the state slots t = 1..T-1,
+   *   Gu[i] u_t <= gu[i]  on every input slot,
+   * Gx [n_sub][n_cx][nx], gx [n_sub][n_cx], Gu [n_sub][n_cu][nu],
+   * gu [n_sub][n_cu], row-major; n_cx, n_cu in 0..DLMPC_MAX_COUPLED (the
+   * pointers may be NULL when the count is 0).  Every row needs a nonzero
+   * normal and g >= 0, so that 0 satisfies the slot's rows and the box.
+   * Rows are normalised to unit normals on upload.  With coupled rows the
+   * Phi-step is the slot QP (as with Q_blk / R_blk); a slot with more than
+   * DLMPC_MAX_REGIONS candidate active sets is rejected. */
+  int32_t n_cx, n_cu;
+  const double *Gx, *gx;
+  const double *Gu, *gu;
 } dlmpc_problem;
+
+#define DLMPC_MAX_COUPLED 4     /* coupled rows per subsystem and slot kind */
+#define DLMPC_MAX_REGIONS 1024  /* active sets (explicit-solution regions) per subsystem and slot kind */
 
 /* Per-instance result of one MPC step. */
 typedef struct {

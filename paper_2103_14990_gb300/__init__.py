@@ -24,6 +24,8 @@ DLMPC_ERR_NONFINITE = -3
 DLMPC_ERR_TIMEOUT = -4
 DLMPC_ERR_CUDA = -5
 DLMPC_ERR_NOMEM = -6
+DLMPC_MAX_COUPLED = 4      # coupled rows per subsystem and slot kind
+DLMPC_MAX_REGIONS = 1024   # explicit-solution regions per subsystem and slot kind
 
 WARM_COLD = 0
 WARM_PREVIOUS = 1
@@ -68,7 +70,9 @@ class Problem_C(ctypes.Structure):
                 ("A_diag", _dp), ("A_off", _dp), ("B", _dp), ("q", _dp), ("r", _dp),
                 ("x_lo", _dp), ("x_hi", _dp), ("u_lo", _dp), ("u_hi", _dp),
                 ("rho", ctypes.c_double), ("eps_p", ctypes.c_double), ("eps_d", ctypes.c_double),
-                ("max_iter", ctypes.c_int32), ("Q_blk", _dp), ("R_blk", _dp)]
+                ("max_iter", ctypes.c_int32), ("Q_blk", _dp), ("R_blk", _dp),
+                ("n_cx", ctypes.c_int32), ("n_cu", ctypes.c_int32),
+                ("Gx", _dp), ("gx", _dp), ("Gu", _dp), ("gu", _dp)]
 
 
 class Stats_C(ctypes.Structure):
@@ -217,6 +221,13 @@ class Solver:
         c.rho, c.eps_p, c.eps_d, c.max_iter = p.rho, p.eps_p, p.eps_d, p.max_iter
         c.Q_blk = _ptr(keep(getattr(p, "Q_blk", None), np.float64), ctypes.c_double)
         c.R_blk = _ptr(keep(getattr(p, "R_blk", None), np.float64), ctypes.c_double)
+        Gx, Gu = getattr(p, "Gx", None), getattr(p, "Gu", None)
+        c.n_cx = 0 if Gx is None else int(Gx.shape[1])
+        c.n_cu = 0 if Gu is None else int(Gu.shape[1])
+        c.Gx = _ptr(keep(Gx, np.float64), ctypes.c_double)
+        c.gx = _ptr(keep(getattr(p, "gx", None) if Gx is not None else None, np.float64), ctypes.c_double)
+        c.Gu = _ptr(keep(Gu, np.float64), ctypes.c_double)
+        c.gu = _ptr(keep(getattr(p, "gu", None) if Gu is not None else None, np.float64), ctypes.c_double)
         return c
 
     def _check(self, rc: int) -> int:

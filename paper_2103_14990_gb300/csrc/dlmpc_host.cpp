@@ -105,6 +105,8 @@ struct Instance {
   std::vector<double> A_diag, A_off, B, q, r, x_lo, x_hi, u_lo, u_hi;
   std::vector<double> Qb, Rb;  // full cost blocks [n_sub][nx][nx], [n_sub][nu][nu] (diag(q), diag(r) if none given)
   bool has_x = false, has_u = false, has_blk = false;
+  int n_cx = 0, n_cu = 0;              // coupled rows per subsystem and slot kind
+  std::vector<double> Gx, gx, Gu, gu;  // unit normals and right-hand sides
   double rho = 1, eps_p = 1e-4, eps_d = 1e-4;
   int max_iter = 1000;
   std::vector<std::vector<int32_t>> patch;  // local ids, ascending
@@ -145,6 +147,15 @@ struct dlmpc_ctx {
   int residency = 2;  // 0: nothing resident, 1: compact iterate, Psi/Lambda and q resident, 2: also N
   int compact = 1;    // iterations after the first of a launch on the compact iterate
   bool block_cost = false;  // some instance has full cost blocks: slot box-QP Phi-step
+  // Explicit solution of the slot QP with coupled rows (some instance has any):
+  // per key 2 * global subsystem + kind (0 state, 1 input) the first region and
+  // the region count, the first constraint row and the row count; per region
+  // its active rows (count in bits 0..3, then 4 bits per row index).
+  bool coupled = false;
+  std::vector<int32_t> h_rg_base, h_rg_cnt, h_rw_base, h_rw_cnt;
+  std::vector<uint32_t> h_rg_desc;
+  std::vector<float> h_crow;  // rows: normal [nmax] then right-hand side
+  int expl_stride = 0, crow_stride = 0;
   int force_block = 0;      // DLMPC_OPT_BLOCK_PHI
   int trace = 0;
   std::vector<int32_t> grp_ptr, grp_items, cta_inst_ptr, cta_inst;
@@ -157,7 +168,9 @@ struct dlmpc_ctx {
   DevBuf<int32_t> d_members, d_rev, d_np, d_grp_ptr, d_grp_items, d_cta_inst_ptr, d_cta_inst, d_adj_ptr, d_adj_idx,
       d_inst_iters, d_err, d_inst_item_ptr, d_sub_off;
   DevBuf<int64_t> d_goff;
-  DevBuf<float> d_qblk2, d_rblk2;
+  DevBuf<float> d_qblk2, d_rblk2, d_crow, d_expl;
+  DevBuf<int32_t> d_rg_base, d_rg_cnt, d_rw_base, d_rw_cnt;
+  DevBuf<uint32_t> d_rg_desc;
   DevBuf<float> d_N, d_q, d_cp, d_psi, d_lam, d_phi, d_G0, d_G1, d_S, d_qw, d_rw, d_xlo, d_xhi, d_ulo, d_uhi, d_rho,
       d_epsp, d_epsd, d_item_r, d_item_s, d_x, d_u, d_xn;
   DevBuf<double> d_Adiag, d_Aoff, d_B;
@@ -263,6 +276,67 @@ void bfs(const Instance &I, int src, int max_hops, std::vector<int> &dist, std::
   }
 }
 
+// Rows A z <= b of the slot polytope of subsystem i (local index) for the
+// slot kind (0: state slots t >= 1, 1: input slots): the finite box bounds as
+// -z_a <= -lo_a, then z_a <= hi_a, then the coupled rows (unit normals).  The
+// slot-0 state has no rows (Z_AB Psi = I pins it).
+void slot_rows(const Instance &I, int nx, int nu, int i, int kind, std::vector<double> &A, std::vector<double> &b) {
+  const int n = kind == 0 ? nx : nu;
+  A.clear();
+  b.clear();
+  const bool box = kind == 0 ? I.has_x : I.has_u;
+  const std::vector<double> &lo = kind == 0 ? I.x_lo : I.u_lo, &hi = kind == 0 ? I.x_hi : I.u_hi;
+  if (box) {
+    for (int side = 0; side < 2; ++side)
+      for (int a = 0; a < n; ++a) {
+        const double v = side == 0 ? lo[(size_t)i * n + a] : hi[(size_t)i * n + a];
+        if (!std::isfinite(v)) continue;
+        for (int c = 0; c < n; ++c) A.push_back(c == a ? (side == 0 ? -1.0 : 1.0) : 0.0);
+        b.push_back(side == 0 ? -v : v);
+      }
+  }
+  const int cnt = kind == 0 ? I.n_cx : I.n_cu;
+  const std::vector<double> &G = kind == 0 ? I.Gx : I.Gu, &g = kind == 0 ? I.gx : I.gu;
+  for (int k = 0; k < cnt; ++k) {
+    for (int a = 0; a < n; ++a) A.push_back(G[((size_t)i * cnt + k) * n + a]);
+    b.push_back(g[(size_t)i * cnt + k]);
+  }
+}
+
+// Candidate active sets of the slot QP (the regions of its piecewise-affine
+// explicit solution): every set of at most n rows with linearly independent
+// normals (Cholesky of the Gram matrix), the empty set first.  Returns false
+// when there are more than DLMPC_MAX_REGIONS.
+bool slot_regions(const std::vector<double> &A, int m, int n, std::vector<uint32_t> &desc) {
+  for (int k = 0; k <= std::min(n, m); ++k)
+    for (uint32_t mask = 0; mask < (1u << m); ++mask) {
+      if (__builtin_popcount(mask) != k) continue;
+      int idx[kMaxNx] = {0}, c = 0;
+      for (int r = 0; r < m; ++r)
+        if (mask >> r & 1u) idx[c++] = r;
+      double L[kMaxNx * kMaxNx] = {0};
+      bool indep = true;
+      for (int a = 0; a < k && indep; ++a)
+        for (int e = 0; e <= a; ++e) {
+          double v = 0;
+          for (int t = 0; t < n; ++t) v += A[(size_t)idx[a] * n + t] * A[(size_t)idx[e] * n + t];
+          for (int t = 0; t < e; ++t) v -= L[a * kMaxNx + t] * L[e * kMaxNx + t];
+          if (a == e) {
+            if (!(v > 1e-10)) { indep = false; break; }
+            L[a * kMaxNx + a] = std::sqrt(v);
+          } else {
+            L[a * kMaxNx + e] = v / L[e * kMaxNx + e];
+          }
+        }
+      if (!indep) continue;
+      uint32_t d = (uint32_t)k;
+      for (int a = 0; a < k; ++a) d |= (uint32_t)idx[a] << (4 + 4 * a);
+      desc.push_back(d);
+      if ((int)desc.size() > DLMPC_MAX_REGIONS) return false;
+    }
+  return true;
+}
+
 int validate(const dlmpc_problem &p, int nx, int nu, std::string &msg) {
   char buf[256];
   if (p.n_sub < 1 || p.nx < 1 || p.nu < 1 || p.nx > kMaxNx || p.nu > kMaxNu || p.T < 2 || p.d < 0) {
@@ -301,6 +375,23 @@ int validate(const dlmpc_problem &p, int nx, int nu, std::string &msg) {
   if (p.x_lo)
     for (int i = 0; i < p.n_sub * nx; ++i)
       if (!(p.x_lo[i] <= 0 && p.x_hi[i] >= 0)) { msg = "0 must lie in [x_lo, x_hi]"; return DLMPC_ERR_ARG; }
+  // coupled rows: counts in range, nonzero finite normals, g >= 0 (0 feasible)
+  if (p.n_cx < 0 || p.n_cx > DLMPC_MAX_COUPLED || p.n_cu < 0 || p.n_cu > DLMPC_MAX_COUPLED) {
+    msg = "n_cx and n_cu must lie in 0..DLMPC_MAX_COUPLED";
+    return DLMPC_ERR_ARG;
+  }
+  for (int kind = 0; kind < 2; ++kind) {
+    const int cnt = kind == 0 ? p.n_cx : p.n_cu, n = kind == 0 ? nx : nu;
+    const double *G = kind == 0 ? p.Gx : p.Gu, *g = kind == 0 ? p.gx : p.gu;
+    if (cnt == 0) continue;
+    if (!G || !g) { msg = "Gx/gx (Gu/gu) must be given when n_cx (n_cu) > 0"; return DLMPC_ERR_ARG; }
+    for (int e = 0; e < p.n_sub * cnt; ++e) {
+      double nrm = 0;
+      for (int a = 0; a < n; ++a) nrm += G[(size_t)e * n + a] * G[(size_t)e * n + a];
+      if (!(nrm > 0) || !std::isfinite(nrm)) { msg = "coupled rows need finite nonzero normals"; return DLMPC_ERR_ARG; }
+      if (!(g[e] >= 0) || !std::isfinite(g[e])) { msg = "coupled right-hand sides must be finite and >= 0"; return DLMPC_ERR_ARG; }
+    }
+  }
   // full cost blocks: symmetric and positive definite (Cholesky must succeed)
   for (int which = 0; which < 2; ++which) {
     const double *blk = which == 0 ? p.Q_blk : p.R_blk;
@@ -464,6 +555,20 @@ extern "C" int dlmpc_setup(const dlmpc_problem *probs, int32_t n_inst, void *str
           I.Rb[((size_t)i * nu + a) * nu + b] =
               p.R_blk ? p.R_blk[((size_t)i * nu + a) * nu + b] : (a == b ? p.r[(size_t)i * nu + a] : 0.0);
     }
+    I.n_cx = p.n_cx;
+    I.n_cu = p.n_cu;
+    for (int kind = 0; kind < 2; ++kind) {
+      const int cnt = kind == 0 ? p.n_cx : p.n_cu, n = kind == 0 ? nx : nu;
+      const double *G = kind == 0 ? p.Gx : p.Gu, *g = kind == 0 ? p.gx : p.gu;
+      std::vector<double> &Go = kind == 0 ? I.Gx : I.Gu, &go = kind == 0 ? I.gx : I.gu;
+      for (int e = 0; e < p.n_sub * cnt; ++e) {
+        double nrm = 0;
+        for (int a = 0; a < n; ++a) nrm += G[(size_t)e * n + a] * G[(size_t)e * n + a];
+        nrm = std::sqrt(nrm);
+        for (int a = 0; a < n; ++a) Go.push_back(G[(size_t)e * n + a] / nrm);
+        go.push_back(g[e] / nrm);
+      }
+    }
     I.has_x = p.x_lo != nullptr;
     I.has_u = p.u_lo != nullptr;
     if (I.has_x) {
@@ -556,6 +661,36 @@ extern "C" int dlmpc_setup(const dlmpc_problem *probs, int32_t n_inst, void *str
   }
   ctx->state_floats = st_off;
   ctx->q_floats = q_off;
+  // regions of the explicit slot-QP solution when some instance has coupled rows
+  for (const Instance &I : ctx->inst) ctx->coupled = ctx->coupled || I.n_cx > 0 || I.n_cu > 0;
+  if (ctx->coupled) {
+    const int nmax = std::max(nx, nu);
+    ctx->expl_stride = nmax * nmax + nmax;
+    ctx->crow_stride = nmax + 1;
+    std::vector<double> A, bb;
+    for (const Instance &I : ctx->inst)
+      for (int i = 0; i < I.n_sub; ++i)
+        for (int kind = 0; kind < 2; ++kind) {
+          const int n = kind == 0 ? nx : nu;
+          slot_rows(I, nx, nu, i, kind, A, bb);
+          const int m = (int)bb.size();
+          ctx->h_rw_base.push_back((int32_t)(ctx->h_crow.size() / ctx->crow_stride));
+          ctx->h_rw_cnt.push_back(m);
+          for (int r = 0; r < m; ++r) {
+            for (int a = 0; a < nmax; ++a) ctx->h_crow.push_back(a < n ? (float)A[(size_t)r * n + a] : 0.f);
+            ctx->h_crow.push_back((float)bb[r]);
+          }
+          std::vector<uint32_t> desc;
+          if (!slot_regions(A, m, n, desc)) {
+            g_setup_error = "a slot has more than DLMPC_MAX_REGIONS candidate active sets";
+            delete ctx;
+            return DLMPC_ERR_ARG;
+          }
+          ctx->h_rg_base.push_back((int32_t)ctx->h_rg_desc.size());
+          ctx->h_rg_cnt.push_back((int32_t)desc.size());
+          ctx->h_rg_desc.insert(ctx->h_rg_desc.end(), desc.begin(), desc.end());
+        }
+  }
   *out = ctx;
   return DLMPC_OK;
 }
@@ -586,7 +721,7 @@ int upload_static(dlmpc_ctx *ctx) {
     }
     for (double v : I.Qb) qblk2.push_back((float)(2.0 * v));
     for (double v : I.Rb) rblk2.push_back((float)(2.0 * v));
-    ctx->block_cost = ctx->block_cost || I.has_blk;
+    ctx->block_cost = ctx->block_cost || I.has_blk || I.n_cx > 0 || I.n_cu > 0;
     Ad.insert(Ad.end(), I.A_diag.begin(), I.A_diag.end());
     Ao.insert(Ao.end(), I.A_off.begin(), I.A_off.end());
     Bm.insert(Bm.end(), I.B.begin(), I.B.end());
@@ -598,6 +733,15 @@ int upload_static(dlmpc_ctx *ctx) {
   CK(upload(ctx->d_qw, qw, s), "upload qw");
   CK(upload(ctx->d_qblk2, qblk2, s), "upload Q blocks");
   CK(upload(ctx->d_rblk2, rblk2, s), "upload R blocks");
+  if (ctx->coupled) {
+    CK(upload(ctx->d_rg_base, ctx->h_rg_base, s), "upload regions");
+    CK(upload(ctx->d_rg_cnt, ctx->h_rg_cnt, s), "upload regions");
+    CK(upload(ctx->d_rw_base, ctx->h_rw_base, s), "upload rows");
+    CK(upload(ctx->d_rw_cnt, ctx->h_rw_cnt, s), "upload rows");
+    CK(upload(ctx->d_rg_desc, ctx->h_rg_desc, s), "upload regions");
+    CK(upload(ctx->d_crow, ctx->h_crow, s), "upload rows");
+    CK(ctx->d_expl.alloc((size_t)ctx->h_rg_desc.size() * ctx->expl_stride), "alloc explicit solution");
+  }
   CK(upload(ctx->d_rw, rw, s), "upload rw");
   CK(upload(ctx->d_xlo, xlo, s), "upload xlo");
   CK(upload(ctx->d_xhi, xhi, s), "upload xhi");
@@ -1139,6 +1283,15 @@ Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_d
   P.block_cost = (ctx->block_cost || ctx->force_block) ? 1 : 0;
   P.qblk2 = ctx->d_qblk2.p;
   P.rblk2 = ctx->d_rblk2.p;
+  P.expl = ctx->coupled ? ctx->d_expl.p : nullptr;
+  P.rg_base = ctx->d_rg_base.p;
+  P.rg_cnt = ctx->d_rg_cnt.p;
+  P.rw_base = ctx->d_rw_base.p;
+  P.rw_cnt = ctx->d_rw_cnt.p;
+  P.rg_desc = ctx->d_rg_desc.p;
+  P.crow = ctx->d_crow.p;
+  P.expl_stride = ctx->expl_stride;
+  P.crow_stride = ctx->crow_stride;
   P.cpst = ctx->d_cp.p;
   return P;
 }

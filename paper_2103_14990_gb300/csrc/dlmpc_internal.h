@@ -110,6 +110,14 @@ struct Params {
   int32_t compact;            // != 0: iterations after the first use the compact iterate
   int32_t block_cost;         // != 0: Phi-step by slot box-QP with the full cost blocks
   const float *qblk2, *rblk2; // [sub][nx][nx] 2 Q_i, [sub][nu][nu] 2 R_i
+  // explicit solution of the slot QP with coupled rows (null: boxes only);
+  // key = 2 * global subsystem + kind (0 state slots, 1 input slots)
+  float *expl;                // [regions][expl_stride]: K [n][n], then k [n] (z = K w + k)
+  const int32_t *rg_base, *rg_cnt;  // per key: first region, region count
+  const int32_t *rw_base, *rw_cnt;  // per key: first constraint row, row count
+  const uint32_t *rg_desc;    // per region: active-row count (bits 0..3), row indices (4 bits each)
+  const float *crow;          // [rows][crow_stride]: unit normal [nmax], right-hand side
+  int32_t expl_stride, crow_stride;
   float *cpst;                // compact iterates of the items without shared-memory residency
 };
 

@@ -336,11 +336,159 @@ __device__ __forceinline__ void slot_box_qp(const float *C, float cd, const floa
   }
 }
 
+// In-place inverse of a symmetric positive definite n x n matrix (n <= kMaxQP),
+// Gauss-Jordan elimination without pivoting (the pivots of an SPD matrix are
+// positive).
+__device__ __forceinline__ void spd_inverse(float (&M)[kMaxQP][kMaxQP], int n) {
+#pragma unroll
+  for (int p = 0; p < kMaxQP; ++p) {
+    if (p < n) {
+      const float inv = 1.f / M[p][p];
+      M[p][p] = 1.f;
+#pragma unroll
+      for (int j = 0; j < kMaxQP; ++j) M[p][j] *= inv;
+#pragma unroll
+      for (int i = 0; i < kMaxQP; ++i) {
+        if (i != p && i < n) {
+          const float f = M[i][p];
+          M[i][p] = 0.f;
+#pragma unroll
+          for (int j = 0; j < kMaxQP; ++j) M[i][j] -= f * M[p][j];
+        }
+      }
+    }
+  }
+}
+
+// Explicit solution of the slot QP, one region (Alg. 1: precomputed from x(tau)
+// once per MPC step).  For the slot QP min 1/2 z^T H z - cd w^T z subject to
+// its rows A z <= b, H = C + cd I (C = 2 Q_i or 2 R_i, cd = rho / s_i), the
+// minimiser on the region's active rows {A_S z = b_S} is affine in w:
+//   z = K w + k,  K = cd (Hi - P M^{-1} P^T),  k = P M^{-1} b_S,
+// with Hi = H^{-1}, P = Hi A_S^T (n x |S|) and M = A_S P (|S| x |S|, SPD
+// since the rows of A_S are independent).  Writes K [n][n] then k [n].
+__device__ void build_region(const Params &P, int sub, int kind, int r, float cd) {
+  const int n = kind == 0 ? P.nx : P.nu;
+  const int key = 2 * sub + kind;
+  const float *C = kind == 0 ? P.qblk2 + (int64_t)sub * n * n : P.rblk2 + (int64_t)sub * n * n;
+  const uint32_t desc = P.rg_desc[P.rg_base[key] + r];
+  const int k = desc & 15u;
+  const float *rows = P.crow + (int64_t)P.rw_base[key] * P.crow_stride;
+  float Hi[kMaxQP][kMaxQP], Pm[kMaxQP][kMaxQP], M[kMaxQP][kMaxQP], bs[kMaxQP];
+#pragma unroll
+  for (int a = 0; a < kMaxQP; ++a)
+#pragma unroll
+    for (int c = 0; c < kMaxQP; ++c) Hi[a][c] = (a < n && c < n) ? C[a * n + c] + (a == c ? cd : 0.f) : 0.f;
+  spd_inverse(Hi, n);
+  // P = Hi A_S^T, b_S
+#pragma unroll
+  for (int j = 0; j < kMaxQP; ++j) {
+    bs[j] = 0.f;
+    const float *aj = rows + (int)((desc >> (4 + 4 * j)) & 15u) * P.crow_stride;
+    if (j < k) bs[j] = aj[P.crow_stride - 1];
+#pragma unroll
+    for (int a = 0; a < kMaxQP; ++a) {
+      float v = 0.f;
+      if (j < k && a < n)
+        for (int c = 0; c < n; ++c) v = fmaf(Hi[a][c], aj[c], v);
+      Pm[a][j] = v;
+    }
+  }
+  // M = A_S P, inverted
+#pragma unroll
+  for (int i = 0; i < kMaxQP; ++i) {
+    const float *ai = rows + (int)((desc >> (4 + 4 * i)) & 15u) * P.crow_stride;
+#pragma unroll
+    for (int j = 0; j < kMaxQP; ++j) {
+      float v = 0.f;
+      if (i < k && j < k)
+        for (int c = 0; c < n; ++c) v = fmaf(ai[c], Pm[c][j], v);
+      M[i][j] = v;
+    }
+  }
+  spd_inverse(M, k);
+  float *out = P.expl + (int64_t)(P.rg_base[key] + r) * P.expl_stride;
+#pragma unroll
+  for (int a = 0; a < kMaxQP; ++a) {
+    if (a >= n) continue;
+    // row a of P M^{-1}
+    float pm[kMaxQP];
+#pragma unroll
+    for (int j = 0; j < kMaxQP; ++j) {
+      float v = 0.f;
+#pragma unroll
+      for (int i = 0; i < kMaxQP; ++i)
+        if (i < k && j < k) v = fmaf(Pm[a][i], M[i][j], v);
+      pm[j] = v;
+    }
+    float kk = 0.f;
+#pragma unroll
+    for (int j = 0; j < kMaxQP; ++j) kk = fmaf(pm[j], bs[j], kk);
+#pragma unroll
+    for (int c = 0; c < kMaxQP; ++c) {
+      if (c >= n) continue;
+      float v = Hi[a][c];
+#pragma unroll
+      for (int j = 0; j < kMaxQP; ++j) v -= pm[j] * Pm[c][j];
+      out[a * n + c] = cd * v;
+    }
+    out[n * n + a] = kk;
+  }
+}
+
+// Evaluates the explicit solution of one slot: among the regions whose affine
+// minimiser z = K w + k satisfies every row of the slot (to a relative 1e-5),
+// the one of least objective 1/2 z^T H z - cd w^T z (the optimum of a strictly
+// convex QP is the minimiser on its own active rows, and no feasible point is
+// lower).  Regions of the slot-0 state: the unconstrained one only.
+__device__ __forceinline__ void slot_explicit(const Params &P, int key, bool slot0, const float *C, float cd,
+                                              const float *w, int n, float *z_out) {
+  const int nreg = slot0 ? 1 : P.rg_cnt[key];
+  const int nrow = slot0 ? 0 : P.rw_cnt[key];
+  const float *tb = P.expl + (int64_t)P.rg_base[key] * P.expl_stride;
+  const float *rows = P.crow + (int64_t)P.rw_base[key] * P.crow_stride;
+  float best = INFINITY;
+  for (int r = 0; r < nreg; ++r, tb += P.expl_stride) {
+    float z[kMaxQP];
+#pragma unroll
+    for (int a = 0; a < kMaxQP; ++a) {
+      z[a] = 0.f;
+      if (a < n) {
+        float v = __ldcg(tb + n * n + a);
+        for (int c = 0; c < n; ++c) v = fmaf(__ldcg(tb + a * n + c), w[c], v);
+        z[a] = v;
+      }
+    }
+    bool ok = true;
+    for (int j = 0; j < nrow && ok; ++j) {
+      const float *aj = rows + j * P.crow_stride;
+      float v = 0.f;
+      for (int c = 0; c < n; ++c) v = fmaf(aj[c], z[c], v);
+      const float bj = aj[P.crow_stride - 1];
+      ok = v <= bj + 1e-5f * fmaxf(1.f, fabsf(bj));
+    }
+    if (!ok) continue;
+    float obj = 0.f;
+    for (int a = 0; a < n; ++a) {
+      float hz = cd * z[a];
+      for (int c = 0; c < n; ++c) hz = fmaf(C[a * n + c], z[c], hz);
+      obj = fmaf(z[a], 0.5f * hz - cd * w[a], obj);
+    }
+    if (obj < best) {
+      best = obj;
+#pragma unroll
+      for (int a = 0; a < kMaxQP; ++a)
+        if (a < n) z_out[a] = z[a];
+    }
+  }
+}
+
 // Phi-comp with full cost blocks Q_i, R_i: the rows of one member at one time
 // slot (its nx state rows or its nu input rows, consecutive in reduced order)
 // share x_hat and are solved together: w per row from the row sums, then
 // min z^T C z + rho/(2 s) ||z - w||^2 over the slot's box (slot_box_qp with
-// H = 2 C + (rho/s) I), alpha = (z - w)/s per row.  One thread per slot.
+// H = 2 C + (rho/s) I) or, with coupled rows, over the slot's polytope
+// (slot_explicit), alpha = (z - w)/s per row.  One thread per slot.
 template <int NX>
 __device__ void phi_slots(const Params &P, const Item &it, const float *tab, const float *rt, const float *Gcur,
                           float *alpha_out, float rho, int gt, int GT) {
@@ -382,7 +530,12 @@ __device__ void phi_slots(const Params &P, const Item &it, const float *tab, con
       z[a] = w[a];
     }
     const float inv_s = rec[2];
-    if (inv_s > 0.f) slot_box_qp(C, rho * inv_s, w, lo, hi, n, z);
+    if (inv_s > 0.f) {
+      if (P.expl)
+        slot_explicit(P, 2 * P.members[it.mem_off + mpos] + (kk < T ? 0 : 1), kk == 0, C, rho * inv_s, w, n, z);
+      else
+        slot_box_qp(C, rho * inv_s, w, lo, hi, n, z);
+    }
 #pragma unroll
     for (int a = 0; a < kMaxQP; ++a) {
       if (a < n) {
@@ -905,6 +1058,15 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
       ++G.phase;
     }
     group_sync(g, GT);
+    if constexpr (BLK) {
+      // explicit solution of the own subsystem's slot QPs for this x(tau)
+      const float s_own = __ldcg(P.S + it.sub);
+      if (P.expl && s_own > 0.f) {
+        const float cd = P.rho_i[it.inst] * (1.f / s_own);
+        const int nrx = P.rg_cnt[2 * it.sub], nr = nrx + P.rg_cnt[2 * it.sub + 1];
+        for (int e = gt; e < nr; e += GT) build_region(P, it.sub, e < nrx ? 0 : 1, e < nrx ? e : e - nrx, cd);
+      }
+    }
     float xj[NX];
 #pragma unroll
     for (int c = 0; c < NX; ++c) xj[c] = P.x[(int64_t)it.sub * NX + c];

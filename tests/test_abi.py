@@ -112,3 +112,79 @@ def test_missing_library_fails_loudly(tmp_path):
             pkg.load_library(str(tmp_path / "nope.so"))
         finally:
             pkg._LIB = pkg._LIB_saved
+
+
+def _with_coupled(n_cx=2, n_cu=1):
+    return I.with_coupled_constraints(I.make_instance(8, 4, 1, seed=4, boxes=True), seed=9, n_cx=n_cx, n_cu=n_cu)
+
+
+def test_setup_validates_coupled_rows(clib):
+    rc, ctx, _ = _setup(clib, [_with_coupled()])
+    assert rc == 0
+    clib.dlmpc_destroy(ctx)
+    rc, ctx, _ = _setup(clib, [_with_coupled(n_cx=pkg.DLMPC_MAX_COUPLED, n_cu=pkg.DLMPC_MAX_COUPLED)])
+    assert rc == 0
+    clib.dlmpc_destroy(ctx)
+    p = _with_coupled(n_cx=pkg.DLMPC_MAX_COUPLED + 1)
+    rc, ctx, _ = _setup(clib, [p])
+    assert rc == pkg.DLMPC_ERR_ARG
+    p = _with_coupled()
+    p.Gx[3, 1] = 0.0                                   # zero normal
+    rc, ctx, _ = _setup(clib, [p])
+    assert rc == pkg.DLMPC_ERR_ARG and b"normal" in clib.dlmpc_last_error(None)
+    p = _with_coupled()
+    p.gu[2, 0] = -0.1                                  # 0 would violate the row
+    rc, ctx, _ = _setup(clib, [p])
+    assert rc == pkg.DLMPC_ERR_ARG
+    p = _with_coupled()
+    p.gx[1, 0] = np.nan
+    rc, ctx, _ = _setup(clib, [p])
+    assert rc == pkg.DLMPC_ERR_ARG
+
+
+def _header_defines():
+    import re
+    out = {}
+    for line in open(os.path.join(ROOT, "include", "dlmpc.h")):
+        m = re.match(r"#define (DLMPC_\w+)\s+\(?(-?\d+)\)?", line)
+        if m:
+            out[m.group(1)] = int(m.group(2))
+    return out
+
+
+def test_binding_constants_match_header():
+    d = _header_defines()
+    assert len(d) >= 20
+    checked = 0
+    for name, v in d.items():
+        short = name[len("DLMPC_"):]
+        for cand in (name, short):
+            if hasattr(pkg, cand):
+                assert getattr(pkg, cand) == v, name
+                checked += 1
+                break
+    assert checked >= 20
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """sizeof and field offsets of the ABI structs as the C compiler lays them
+    out, against the binding's ctypes structures."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in pkg.Problem_C._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dlmpc.h"', "int main(void) {",
+             '  printf("%zu\\n", sizeof(dlmpc_problem));']
+    lines += ['  printf("%%zu\\n", offsetof(dlmpc_problem, %s));' % f for f in fields]
+    lines += ['  printf("%zu\\n", sizeof(dlmpc_stats));', "  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert vals[0] == ctypes.sizeof(pkg.Problem_C)
+    for f, off in zip(fields, vals[1:1 + len(fields)]):
+        assert getattr(pkg.Problem_C, f).offset == off, f
+    assert vals[-1] == ctypes.sizeof(pkg.Stats_C)

@@ -8,6 +8,8 @@ Parity modes:
            entry scaled by ||u||) and the iteration counts reported.
 Every call goes through the C ABI (libdlmpc.so) via the ctypes binding.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -453,3 +455,123 @@ def test_operator_checkpoint_round_trip(torch):
         b2.import_operators(blob[:-8])
     for s in (a, b, other):
         s.close()
+
+
+# --------------------------------------------------------------------------
+# Coupled per-slot constraints (Gx x_t <= gx, Gu u_t <= gu beside the boxes):
+# the explicit slot-QP solution, rebuilt from x(tau) in the sweep's prologue
+# at every MPC step, against the oracle's active-set enumeration
+# --------------------------------------------------------------------------
+
+def binding_rows(p, z):
+    """Coupled rows active (to 1e-6) at the slot values z of the oracle."""
+    nb = 0
+    for i in range(p.n_sub):
+        for t in range(1, p.T):
+            rr = [O.global_row(p, i, t * p.nx + a) for a in range(p.nx)]
+            if p.Gx is not None:
+                nb += int(np.sum(p.Gx[i] @ z[rr] - p.gx[i] > -1e-6))
+        for t in range(p.T - 1):
+            rr = [O.global_row(p, i, p.nx * p.T + t * p.nu + b) for b in range(p.nu)]
+            if p.Gu is not None:
+                nb += int(np.sum(p.Gu[i] @ z[rr] - p.gu[i] > -1e-6))
+    return nb
+
+
+COUPLED = {
+    "chain16_T10_d3_box_cpl": lambda: I.with_coupled_constraints(
+        I.make_instance(16, 10, 3, seed=1, boxes=True, x0_dist="uniform"), seed=51, n_cx=2, n_cu=1),
+    "grid5x5_T6_d2_box_cpl": lambda: I.with_coupled_constraints(
+        I.make_instance(25, 6, 2, graph="grid", seed=2, boxes=True), seed=52, n_cx=2),
+    "chain10_nobox_cpl4": lambda: I.with_coupled_constraints(I.chain10(), seed=53, n_cx=4, n_cu=2,
+                                                             g_range=(0.2, 0.6)),
+}
+
+
+@pytest.mark.parametrize("name", list(COUPLED))
+@pytest.mark.parametrize("K", [1, 7, 60])
+def test_coupled_fixed_iterations_parity(name, K, torch):
+    """Phi, Psi, Lambda and u after K iterations (full form with Phi export,
+    and the compact iterate) against the oracle's slot QP with coupled rows."""
+    p = COUPLED[name]()
+    o = O.Oracle(p)
+    ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=K)
+    if K == 60:
+        assert binding_rows(p, ref.z) > 0, "the coupled rows must bind"
+    s = gpu_solver([p], torch)
+    rc, st, phi, psi, lam, u, xn = run_fixed(s, torch, p.x0, K)
+    assert rel(psi, ref.Psi) <= REL and rel(phi, ref.Phi) <= REL
+    assert rel(lam, ref.Lam) <= REL or np.linalg.norm(ref.Lam) < 1e-6
+    u_ref = o.control(ref)
+    assert rel(u, u_ref) <= REL or np.max(np.abs(u - u_ref)) < 1e-7
+    rc, st, _, psi2, lam2, u2, _ = run_fixed(s, torch, p.x0, K, export=False)
+    assert rel(psi2, ref.Psi) <= REL
+    assert rel(lam2, ref.Lam) <= REL or np.linalg.norm(ref.Lam) < 1e-6
+    assert rel(u2, u_ref) <= REL or np.max(np.abs(u2 - u_ref)) < 1e-7
+    s.close()
+
+
+def test_coupled_stopped_closed_loop(torch):
+    """Conv on, warm start from the previous step: u(tau) of every MPC step
+    and the iteration counts against the oracle's closed loop (a feasible
+    instance whose coupled rows bind at the first step)."""
+    import paper_2103_14990_gb300 as pkg
+    base = I.make_instance(4, 4, 1, seed=3, boxes=True, x0_dist="uniform", x_bound=1.0, u_bound=0.5, mpc_steps=4)
+    base.x0 = 0.3 * base.x0
+    p = dataclasses.replace(I.with_coupled_constraints(base, seed=8, n_cx=2, g_range=(0.1, 0.3)), max_iter=3000)
+    o = O.Oracle(p)
+    first = O.admm(o.lay, o.blocks, p.x0)
+    assert binding_rows(p, first.z) > 0
+    xs, us, its, _ = o.run_mpc(p.mpc_steps, warm="previous")
+    s = gpu_solver([p], torch)
+    worst = 0.0
+    for tau in range(p.mpc_steps):
+        x = torch.tensor(xs[tau].astype(np.float32), device="cuda")
+        u = torch.zeros(p.n_sub, 1, device="cuda")
+        rc, st = s.step(x, u, None, warm=pkg.WARM_PREVIOUS if tau > 0 else pkg.WARM_COLD)
+        assert st[0]["status"] == 0
+        assert abs(st[0]["iters"] - its[tau]) <= max(3, 0.05 * its[tau])
+        worst = max(worst, rel(u.cpu().numpy(), us[tau]))
+    assert worst <= 5 * REL
+    s.close()
+
+
+def test_slack_coupled_rows_match_the_box_slot_qp(torch):
+    """Coupled rows that can never bind (g = 100) leave the slot QP a box-QP:
+    the explicit solution gives what the box solver gives."""
+    base = I.with_block_costs(I.make_instance(16, 10, 3, seed=1, boxes=True, x0_dist="uniform"), seed=31)
+    cpl = I.with_coupled_constraints(base, seed=54, n_cx=2, n_cu=1)
+    cpl = dataclasses.replace(cpl, gx=np.full_like(cpl.gx, 100.0), gu=np.full_like(cpl.gu, 100.0))
+    outs = []
+    for p in (base, cpl):
+        s = gpu_solver([p], torch)
+        outs.append(run_fixed(s, torch, p.x0, 40))
+        s.close()
+    (_, _, phi_a, psi_a, _, u_a, _), (_, _, phi_b, psi_b, _, u_b, _) = outs
+    assert rel(phi_b, phi_a) <= 1e-5 and rel(psi_b, psi_a) <= 1e-5
+    assert rel(u_b, u_a) <= 1e-5 or np.max(np.abs(u_a - u_b)) < 1e-7
+
+
+def test_coupled_in_a_batch_with_a_plain_instance(torch):
+    """Two instances in one context, one with coupled rows and one without:
+    each against its own oracle run (the plain one through the slot QP of its
+    boxes)."""
+    a = COUPLED["grid5x5_T6_d2_box_cpl"]()
+    b = I.make_instance(16, 10, 3, seed=1, boxes=True, x0_dist="uniform")
+    K = 25
+    s = gpu_solver([a, b], torch)
+    x0 = np.concatenate([a.x0, b.x0])
+    rc, st, phi, psi, lam, u, xn = run_fixed(s, torch, x0, K)
+    off_s = 0
+    off_u = 0
+    for p in (a, b):
+        o = O.Oracle(p)
+        ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=K)
+        n = ref.Psi.size
+        assert rel(psi[off_s:off_s + n], ref.Psi) <= REL
+        u_ref = o.control(ref)
+        uu = u[off_u:off_u + p.n_sub]
+        assert rel(uu, u_ref) <= REL or np.max(np.abs(uu - u_ref)) < 1e-7
+        off_s += n
+        off_u += p.n_sub
+    s.close()
