@@ -42,14 +42,24 @@ NCU_TRAFFIC = {"workload": "chain1024", "src_sha256": "211b291e8ad858e1da2700038
                "bytes_per_launch": 85987328}  # profiles/sweep_kernel_chain1024.md
 
 
-def workload(name: str):
+INNER_QP = {"box": "diagonal Q, R with boxes (closed-form row Phi-step)",
+            "block": "full SPD Q_i, R_i with boxes (slot box-QP)",
+            "coupled": "full SPD Q_i, R_i, boxes and 2 coupled state rows per slot (explicit slot-QP solution)"}
+
+
+def workload(name: str, inner_qp: str = "box"):
     from paper_2103_14990_gb300 import instances as I
-    return {"chain1024": I.chain1024, "chain10": I.chain10, "grid64": I.grid64}[name]()
+    p = {"chain1024": I.chain1024, "chain10": I.chain10, "grid64": I.grid64}[name]()
+    if inner_qp == "block":
+        p = I.with_block_costs(p, seed=101)
+    elif inner_qp == "coupled":
+        p = I.with_coupled_constraints(p, seed=102, n_cx=2, n_cu=0, g_range=(0.8, 1.2))
+    return p
 
 
-def bench_config(prob, world: int) -> dict:
+def bench_config(prob, world: int, inner_qp: str = "box") -> dict:
     """The workload description shared by both arms."""
-    return {"workload": prob.name, "n_sub": prob.n_sub, "T": prob.T, "d": prob.d, "boxes": "|x|<=1, |u|<=2",
+    return {"workload": prob.name, "inner_qp": INNER_QP[inner_qp], "n_sub": prob.n_sub, "T": prob.T, "d": prob.d, "boxes": "|x|<=1, |u|<=2",
             "warm_start": "previous MPC step's Psi/Lambda (step 0 cold)", "max_iter": prob.max_iter,
             "eps": prob.eps_p, "l2": "flushed between steps (256 MiB write outside the events)",
             "parallelism": "replicas" if world > 1 else "single GPU"}
@@ -154,7 +164,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    prob = workload(args.workload)
+    prob = workload(args.workload, args.inner_qp)
     t_setup = time.time()
     solver = pkg.Solver([prob])
     torch.cuda.synchronize()
@@ -217,7 +227,7 @@ def run_ours(args):
 
     # ablation of the paper's GPU mappings (Sec. III): ADMM iterations/s from x(0)
     ablation = {}
-    if not args.no_ablation:
+    if not args.no_ablation and args.inner_qp == "box":  # the paper's mappings take diagonal weights
         names = {0: "naive (Sec. III-A)", 1: "combined (Sec. III-C)", 2: "persistent column patch (this library)"}
         for v, it_n in ((0, args.ablation_iters), (1, args.ablation_iters), (2, 10 * args.ablation_iters)):
             solver.run_variant(v, x0, 2)  # warm-up
@@ -227,7 +237,8 @@ def run_ours(args):
         for v in ablation.values():
             v["speedup_vs_naive"] = round(v["admm_iters_per_s"] / base, 2)
 
-    learned = learned_line(prob, args) if (not args.no_learned and rank == 0 and world == 1) else None
+    learned = (learned_line(prob, args)
+               if (not args.no_learned and rank == 0 and world == 1 and args.inner_qp == "box") else None)
 
     # e2e: host (pinned) buffers through the C ABI, H2D and D2H inside the timed region
     xh = torch.empty(n, nx, dtype=torch.float32, pin_memory=True)
@@ -248,7 +259,8 @@ def run_ours(args):
     peak, peak_src = measured_peaks()
     achieved = info["iter_bytes"] * tot_iters / kern_s / 1e9
     traffic = (NCU_TRAFFIC["bytes_per_launch"]
-               if NCU_TRAFFIC["src_sha256"] == kernel_sha() and NCU_TRAFFIC["workload"] == args.workload else None)
+               if NCU_TRAFFIC["src_sha256"] == kernel_sha() and NCU_TRAFFIC["workload"] == args.workload
+               and args.inner_qp == "box" else None)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_src, "kernel": "sweep_kernel",
@@ -260,7 +272,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_dev / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded chain plant, x0 ~ U[-0.9,0.9])",
-        "config": bench_config(prob, world),
+        "config": bench_config(prob, world, args.inner_qp),
         "admm_iters_per_s": round(tot_iters / kern_s, 1),
         "iters_per_step": round(tot_iters / args.steps, 2),
         "steps_at_max_iter": int(sum(1 for s in status if s != 0)),
@@ -280,7 +292,7 @@ def run_ours(args):
         "wall_s_timed_region": round(wall, 4),
         "clocks": clk.summary(),
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.inner_qp == "box":
         out["cpu_baseline"] = cpu_baseline(args, iters)
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -417,7 +429,7 @@ def run_reference(args):
     from oracle import dlmpc_oracle as O
     prob = workload(args.workload)
     o = O.Oracle(prob)
-    table = oracle_iters_table(args.workload)
+    table = oracle_iters_table(args.workload) if args.inner_qp == "box" else None
     if table is None:
         print(json.dumps({"impl": "reference", "unavailable": "no oracle iteration table for this workload"}))
         return
@@ -460,6 +472,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="chain1024")
+    ap.add_argument("--inner-qp", choices=sorted(INNER_QP), default="box",
+                    help="Phi-step cost/constraint form: box (default), block, coupled")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")

@@ -665,7 +665,7 @@ extern "C" int dlmpc_setup(const dlmpc_problem *probs, int32_t n_inst, void *str
   for (const Instance &I : ctx->inst) ctx->coupled = ctx->coupled || I.n_cx > 0 || I.n_cu > 0;
   if (ctx->coupled) {
     const int nmax = std::max(nx, nu);
-    ctx->expl_stride = nmax * nmax + nmax;
+    ctx->expl_stride = 2 * (nmax * nmax + nmax);  // K, k, L, l
     ctx->crow_stride = nmax + 1;
     std::vector<double> A, bb;
     for (const Instance &I : ctx->inst)

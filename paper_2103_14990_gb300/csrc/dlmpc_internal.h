@@ -112,7 +112,7 @@ struct Params {
   const float *qblk2, *rblk2; // [sub][nx][nx] 2 Q_i, [sub][nu][nu] 2 R_i
   // explicit solution of the slot QP with coupled rows (null: boxes only);
   // key = 2 * global subsystem + kind (0 state slots, 1 input slots)
-  float *expl;                // [regions][expl_stride]: K [n][n], then k [n] (z = K w + k)
+  float *expl;                // [regions][expl_stride]: K [n][n], k [n], L [n][n], l [n] (z = K w + k, mu = L w + l)
   const int32_t *rg_base, *rg_cnt;  // per key: first region, region count
   const int32_t *rw_base, *rw_cnt;  // per key: first constraint row, row count
   const uint32_t *rg_desc;    // per region: active-row count (bits 0..3), row indices (4 bits each)

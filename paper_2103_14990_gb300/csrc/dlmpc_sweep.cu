@@ -220,7 +220,8 @@ __device__ __forceinline__ void phi_row(const Params &P, int p, int dred, int au
 // Psi_r - Lambda_r + alpha x_hat; only alpha is stored, in reduced order
 // (the reduced rows, then the slot-0 rows).  A thread takes two rows at a
 // time and issues the exchange loads of both before adding them.
-template <int GT>
+// W_ONLY: store w itself (the block Phi-step solves the slots afterwards).
+template <int GT, bool W_ONLY = false>
 __device__ __forceinline__ void phi_rows(const Params &P, const Item &it, const float *rt, const float *Gcur,
                                          float *alpha_out, int gt) {
   const int r_sub = it.r_sub;
@@ -252,108 +253,126 @@ __device__ __forceinline__ void phi_rows(const Params &P, const Item &it, const 
         w2 += gv2[j];
       }
     }
-    phi_row(P, p, it.dred, ia.w, ca, w, alpha_out);
-    if (two) phi_row(P, p2, it.dred, ib.w, cb, w2, alpha_out);
+    if constexpr (W_ONLY) {
+      alpha_out[p] = w;
+      if (two) alpha_out[p2] = w2;
+    } else {
+      phi_row(P, p, it.dred, ia.w, ca, w, alpha_out);
+      if (two) phi_row(P, p2, it.dred, ib.w, cb, w2, alpha_out);
+    }
   }
 }
 
-// argmin 1/2 z^T (C + cd I) z - cd w^T z  s.t.  lo <= z <= hi  (n <= kMaxQP,
-// C symmetric positive semi-definite, cd > 0): every component free, at lo or
-// at hi (finite bounds only); the free part solves its linear system
-// (Gaussian elimination, the matrix is positive definite), and among the
-// feasible candidates the one of least objective is the optimum (the optimum
-// of a strictly convex QP is one of them, and no feasible point is lower).
 constexpr int kMaxQP = 4;
 
-__device__ __forceinline__ void slot_box_qp(const float *C, float cd, const float *w, const float *lo,
-                                            const float *hi, int n, float *z_out) {
+// argmin 1/2 z^T (C + cd I) z - cd w^T z  s.t.  lo <= z <= hi  (N <= kMaxQP,
+// C symmetric positive semi-definite, cd > 0): every component free, at lo or
+// at hi (finite bounds only).  A pattern's candidate solves the N x N system
+// whose free rows are those of C + cd I (right-hand side cd w) and whose fixed
+// rows are z_a = bound, by elimination without pivoting (the fixed rows are
+// unit rows and the free pivots are Schur complements of a positive definite
+// matrix).  The first feasible candidate whose gradient has the KKT signs on
+// its fixed components is the optimum; should rounding let none pass, the
+// feasible candidate of least objective is taken (the optimum of a strictly
+// convex QP is one of them, and no feasible point is lower).
+template <int N>
+__device__ __forceinline__ void slot_box_qp(const float *C, float cd, const float (&w)[N], const float (&lo)[N],
+                                            const float (&hi)[N], float (&z_out)[N]) {
+  constexpr int kPat = N == 1 ? 3 : N == 2 ? 9 : N == 3 ? 27 : 81;
   float best = INFINITY;
-  int npat = 1;
-  for (int a = 0; a < n; ++a) npat *= 3;
-  for (int pat = 0; pat < npat; ++pat) {
-    int d[kMaxQP];
+#pragma unroll 1
+  for (int pat = 0; pat < kPat; ++pat) {
+    int d[N];
     bool ok = true;
     int rem = pat;
 #pragma unroll
-    for (int a = 0; a < kMaxQP; ++a) {
-      d[a] = 0;
-      if (a < n) {
-        d[a] = rem % 3;
-        rem /= 3;
-        if ((d[a] == 1 && !(lo[a] > -INFINITY)) || (d[a] == 2 && !(hi[a] < INFINITY))) ok = false;
-      }
+    for (int a = 0; a < N; ++a) {
+      d[a] = rem % 3;
+      rem /= 3;
+      if ((d[a] == 1 && !(lo[a] > -INFINITY)) || (d[a] == 2 && !(hi[a] < INFINITY))) ok = false;
     }
     if (!ok) continue;
-    float z[kMaxQP], M[kMaxQP][kMaxQP + 1];
-    int fi[kMaxQP];
-    int m = 0;
+    float M[N][N + 1];
 #pragma unroll
-    for (int a = 0; a < kMaxQP; ++a) {
-      z[a] = 0.f;
-      if (a < n && d[a] != 0) z[a] = d[a] == 1 ? lo[a] : hi[a];
+    for (int a = 0; a < N; ++a) {
+#pragma unroll
+      for (int c = 0; c < N; ++c)
+        M[a][c] = d[a] == 0 ? C[a * N + c] + (a == c ? cd : 0.f) : (a == c ? 1.f : 0.f);
+      M[a][N] = d[a] == 0 ? cd * w[a] : (d[a] == 1 ? lo[a] : hi[a]);
     }
 #pragma unroll
-    for (int a = 0; a < kMaxQP; ++a)
-      if (a < n && d[a] == 0) fi[m++] = a;
-    // M [m x m | rhs]: (C + cd I)_FF z_F = cd w_F - (C)_FA z_A
-    for (int i = 0; i < m; ++i) {
-      const int a = fi[i];
-      float rhs = cd * w[a];
-      for (int b = 0; b < n; ++b)
-        if (d[b] != 0) rhs -= C[a * n + b] * z[b];
-      for (int j = 0; j < m; ++j) M[i][j] = C[a * n + fi[j]] + (i == j ? cd : 0.f);
-      M[i][m] = rhs;
-    }
-    for (int i = 0; i < m; ++i) {
-      const float inv = 1.f / M[i][i];
-      for (int r = i + 1; r < m; ++r) {
-        const float f = M[r][i] * inv;
-        for (int j = i; j <= m; ++j) M[r][j] -= f * M[i][j];
+    for (int q = 0; q < N; ++q) {
+      const float inv = 1.f / M[q][q];
+#pragma unroll
+      for (int r = q + 1; r < N; ++r) {
+        const float f = M[r][q] * inv;
+#pragma unroll
+        for (int c = q; c <= N; ++c) M[r][c] -= f * M[q][c];
       }
     }
-    for (int i = m - 1; i >= 0; --i) {
-      float v = M[i][m];
-      for (int j = i + 1; j < m; ++j) v -= M[i][j] * z[fi[j]];
-      z[fi[i]] = v / M[i][i];
+    float z[N];
+#pragma unroll
+    for (int a = N - 1; a >= 0; --a) {
+      float v = M[a][N];
+#pragma unroll
+      for (int c = a + 1; c < N; ++c) v -= M[a][c] * z[c];
+      z[a] = v / M[a][a];
     }
-    for (int i = 0; i < m && ok; ++i) {
-      const int a = fi[i];
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
       const float tol_lo = 1e-5f * fmaxf(1.f, fabsf(lo[a])), tol_hi = 1e-5f * fmaxf(1.f, fabsf(hi[a]));
       if (z[a] < lo[a] - tol_lo || z[a] > hi[a] + tol_hi) ok = false;
       z[a] = fminf(fmaxf(z[a], lo[a]), hi[a]);
     }
     if (!ok) continue;
+    // KKT signs of the gradient g = H z - cd w on the fixed components
+    // (g >= 0 at lo, g <= 0 at hi, to a relative 1e-5): the optimum at once
+    bool kkt = true;
     float obj = 0.f;
-    for (int a = 0; a < n; ++a) {
-      float hz = cd * z[a];
-      for (int b = 0; b < n; ++b) hz = fmaf(C[a * n + b], z[b], hz);
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      float hz = cd * z[a], mag = fabsf(cd * z[a]) + fabsf(cd * w[a]);
+#pragma unroll
+      for (int c = 0; c < N; ++c) {
+        hz = fmaf(C[a * N + c], z[c], hz);
+        mag = fmaf(fabsf(C[a * N + c]), fabsf(z[c]), mag);
+      }
+      const float g = hz - cd * w[a], tol = 1e-5f * mag;
+      if ((d[a] == 1 && g < -tol) || (d[a] == 2 && g > tol)) kkt = false;
       obj = fmaf(z[a], 0.5f * hz - cd * w[a], obj);
+    }
+    if (kkt) {
+#pragma unroll
+      for (int a = 0; a < N; ++a) z_out[a] = z[a];
+      return;
     }
     if (obj < best) {
       best = obj;
-      for (int a = 0; a < n; ++a) z_out[a] = z[a];
+#pragma unroll
+      for (int a = 0; a < N; ++a) z_out[a] = z[a];
     }
   }
 }
 
-// In-place inverse of a symmetric positive definite n x n matrix (n <= kMaxQP),
+// In-place inverse of a symmetric positive definite matrix of order k <= N,
 // Gauss-Jordan elimination without pivoting (the pivots of an SPD matrix are
 // positive).
-__device__ __forceinline__ void spd_inverse(float (&M)[kMaxQP][kMaxQP], int n) {
+template <int N>
+__device__ __forceinline__ void spd_inverse(float (&M)[N][N], int k) {
 #pragma unroll
-  for (int p = 0; p < kMaxQP; ++p) {
-    if (p < n) {
+  for (int p = 0; p < N; ++p) {
+    if (p < k) {
       const float inv = 1.f / M[p][p];
       M[p][p] = 1.f;
 #pragma unroll
-      for (int j = 0; j < kMaxQP; ++j) M[p][j] *= inv;
+      for (int j = 0; j < N; ++j) M[p][j] *= inv;
 #pragma unroll
-      for (int i = 0; i < kMaxQP; ++i) {
-        if (i != p && i < n) {
+      for (int i = 0; i < N; ++i) {
+        if (i != p && i < k) {
           const float f = M[i][p];
           M[i][p] = 0.f;
 #pragma unroll
-          for (int j = 0; j < kMaxQP; ++j) M[i][j] -= f * M[p][j];
+          for (int j = 0; j < N; ++j) M[i][j] -= f * M[p][j];
         }
       }
     }
@@ -363,185 +382,234 @@ __device__ __forceinline__ void spd_inverse(float (&M)[kMaxQP][kMaxQP], int n) {
 // Explicit solution of the slot QP, one region (Alg. 1: precomputed from x(tau)
 // once per MPC step).  For the slot QP min 1/2 z^T H z - cd w^T z subject to
 // its rows A z <= b, H = C + cd I (C = 2 Q_i or 2 R_i, cd = rho / s_i), the
-// minimiser on the region's active rows {A_S z = b_S} is affine in w:
-//   z = K w + k,  K = cd (Hi - P M^{-1} P^T),  k = P M^{-1} b_S,
-// with Hi = H^{-1}, P = Hi A_S^T (n x |S|) and M = A_S P (|S| x |S|, SPD
-// since the rows of A_S are independent).  Writes K [n][n] then k [n].
+// minimiser on the region's active rows {A_S z = b_S} and its multipliers are
+// affine in w:
+//   z  = K w + k,   K = cd (Hi - P M^{-1} P^T),  k = P M^{-1} b_S,
+//   mu = L w + l,   L = cd M^{-1} P^T,           l = -M^{-1} b_S,
+// with Hi = H^{-1}, P = Hi A_S^T (N x |S|) and M = A_S P (|S| x |S|, SPD since
+// the rows of A_S are independent).  Writes K [N][N], k [N], L [N][N] (rows
+// below |S| used), l [N].
+template <int N>
 __device__ void build_region(const Params &P, int sub, int kind, int r, float cd) {
-  const int n = kind == 0 ? P.nx : P.nu;
   const int key = 2 * sub + kind;
-  const float *C = kind == 0 ? P.qblk2 + (int64_t)sub * n * n : P.rblk2 + (int64_t)sub * n * n;
+  const float *C = kind == 0 ? P.qblk2 + (int64_t)sub * N * N : P.rblk2 + (int64_t)sub * N * N;
   const uint32_t desc = P.rg_desc[P.rg_base[key] + r];
   const int k = desc & 15u;
-  const float *rows = P.crow + (int64_t)P.rw_base[key] * P.crow_stride;
-  float Hi[kMaxQP][kMaxQP], Pm[kMaxQP][kMaxQP], M[kMaxQP][kMaxQP], bs[kMaxQP];
+  const int cs = P.crow_stride;
+  const float *rows = P.crow + (int64_t)P.rw_base[key] * cs;
+  float Hi[N][N], Pm[N][N], M[N][N], bs[N];
 #pragma unroll
-  for (int a = 0; a < kMaxQP; ++a)
+  for (int a = 0; a < N; ++a)
 #pragma unroll
-    for (int c = 0; c < kMaxQP; ++c) Hi[a][c] = (a < n && c < n) ? C[a * n + c] + (a == c ? cd : 0.f) : 0.f;
-  spd_inverse(Hi, n);
+    for (int c = 0; c < N; ++c) Hi[a][c] = C[a * N + c] + (a == c ? cd : 0.f);
+  spd_inverse<N>(Hi, N);
   // P = Hi A_S^T, b_S
 #pragma unroll
-  for (int j = 0; j < kMaxQP; ++j) {
-    bs[j] = 0.f;
-    const float *aj = rows + (int)((desc >> (4 + 4 * j)) & 15u) * P.crow_stride;
-    if (j < k) bs[j] = aj[P.crow_stride - 1];
+  for (int j = 0; j < N; ++j) {
+    const float *aj = rows + (int)((desc >> (4 + 4 * j)) & 15u) * cs;
+    bs[j] = j < k ? aj[cs - 1] : 0.f;
 #pragma unroll
-    for (int a = 0; a < kMaxQP; ++a) {
+    for (int a = 0; a < N; ++a) {
       float v = 0.f;
-      if (j < k && a < n)
-        for (int c = 0; c < n; ++c) v = fmaf(Hi[a][c], aj[c], v);
+      if (j < k)
+#pragma unroll
+        for (int c = 0; c < N; ++c) v = fmaf(Hi[a][c], aj[c], v);
       Pm[a][j] = v;
     }
   }
   // M = A_S P, inverted
 #pragma unroll
-  for (int i = 0; i < kMaxQP; ++i) {
-    const float *ai = rows + (int)((desc >> (4 + 4 * i)) & 15u) * P.crow_stride;
+  for (int i = 0; i < N; ++i) {
+    const float *ai = rows + (int)((desc >> (4 + 4 * i)) & 15u) * cs;
 #pragma unroll
-    for (int j = 0; j < kMaxQP; ++j) {
+    for (int j = 0; j < N; ++j) {
       float v = 0.f;
       if (i < k && j < k)
-        for (int c = 0; c < n; ++c) v = fmaf(ai[c], Pm[c][j], v);
+#pragma unroll
+        for (int c = 0; c < N; ++c) v = fmaf(ai[c], Pm[c][j], v);
       M[i][j] = v;
     }
   }
-  spd_inverse(M, k);
-  float *out = P.expl + (int64_t)(P.rg_base[key] + r) * P.expl_stride;
+  spd_inverse<N>(M, k);
+  // Q = M^{-1} P^T (|S| x N): the multiplier map over cd
+  float Qm[N][N];
 #pragma unroll
-  for (int a = 0; a < kMaxQP; ++a) {
-    if (a >= n) continue;
-    // row a of P M^{-1}
-    float pm[kMaxQP];
+  for (int j = 0; j < N; ++j)
 #pragma unroll
-    for (int j = 0; j < kMaxQP; ++j) {
+    for (int c = 0; c < N; ++c) {
       float v = 0.f;
 #pragma unroll
-      for (int i = 0; i < kMaxQP; ++i)
-        if (i < k && j < k) v = fmaf(Pm[a][i], M[i][j], v);
-      pm[j] = v;
+      for (int i = 0; i < N; ++i)
+        if (i < k && j < k) v = fmaf(M[j][i], Pm[c][i], v);
+      Qm[j][c] = v;
     }
-    float kk = 0.f;
+  float *out = P.expl + (int64_t)(P.rg_base[key] + r) * P.expl_stride;
 #pragma unroll
-    for (int j = 0; j < kMaxQP; ++j) kk = fmaf(pm[j], bs[j], kk);
+  for (int a = 0; a < N; ++a) {
+    // (P M^{-1})[a][j] = Qm[j][a] (M^{-1} is symmetric)
+    float kk = 0.f, lj = 0.f;
 #pragma unroll
-    for (int c = 0; c < kMaxQP; ++c) {
-      if (c >= n) continue;
+    for (int j = 0; j < N; ++j) kk = fmaf(Qm[j][a], bs[j], kk);
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
       float v = Hi[a][c];
 #pragma unroll
-      for (int j = 0; j < kMaxQP; ++j) v -= pm[j] * Pm[c][j];
-      out[a * n + c] = cd * v;
+      for (int j = 0; j < N; ++j) v -= Qm[j][a] * Pm[c][j];
+      out[a * N + c] = cd * v;
+      out[N * N + N + a * N + c] = cd * Qm[a][c];
     }
-    out[n * n + a] = kk;
+#pragma unroll
+    for (int i = 0; i < N; ++i) lj = fmaf(M[a][i], bs[i], lj);
+    out[N * N + a] = kk;
+    out[2 * N * N + N + a] = -lj;
   }
 }
 
-// Evaluates the explicit solution of one slot: among the regions whose affine
-// minimiser z = K w + k satisfies every row of the slot (to a relative 1e-5),
-// the one of least objective 1/2 z^T H z - cd w^T z (the optimum of a strictly
-// convex QP is the minimiser on its own active rows, and no feasible point is
-// lower).  Regions of the slot-0 state: the unconstrained one only.
+// Evaluates the explicit solution of one slot, region by region in the
+// order of the setup (active sets by size, the empty one first): the first
+// region whose minimiser z = K w + k satisfies every row of the slot and whose
+// multipliers mu = L w + l are non-negative (both to a relative 1e-5) is the
+// optimum.  Should rounding let none pass, the feasible region of least
+// objective 1/2 z^T H z - cd w^T z is taken (the optimum of a strictly convex
+// QP is the minimiser on its own active rows, and no feasible point is lower).
+// The slot-0 state has the empty region only.
+template <int N>
 __device__ __forceinline__ void slot_explicit(const Params &P, int key, bool slot0, const float *C, float cd,
-                                              const float *w, int n, float *z_out) {
+                                              const float (&w)[N], float (&z_out)[N]) {
   const int nreg = slot0 ? 1 : P.rg_cnt[key];
   const int nrow = slot0 ? 0 : P.rw_cnt[key];
-  const float *tb = P.expl + (int64_t)P.rg_base[key] * P.expl_stride;
-  const float *rows = P.crow + (int64_t)P.rw_base[key] * P.crow_stride;
+  const int cs = P.crow_stride;
+  const int base = P.rg_base[key];
+  const float *tb = P.expl + (int64_t)base * P.expl_stride;
+  const float *rows = P.crow + (int64_t)P.rw_base[key] * cs;
   float best = INFINITY;
+#pragma unroll 1
   for (int r = 0; r < nreg; ++r, tb += P.expl_stride) {
-    float z[kMaxQP];
+    float z[N];
 #pragma unroll
-    for (int a = 0; a < kMaxQP; ++a) {
-      z[a] = 0.f;
-      if (a < n) {
-        float v = __ldcg(tb + n * n + a);
-        for (int c = 0; c < n; ++c) v = fmaf(__ldcg(tb + a * n + c), w[c], v);
-        z[a] = v;
-      }
+    for (int a = 0; a < N; ++a) {
+      float v = __ldcg(tb + N * N + a);
+#pragma unroll
+      for (int c = 0; c < N; ++c) v = fmaf(__ldcg(tb + a * N + c), w[c], v);
+      z[a] = v;
     }
     bool ok = true;
-    for (int j = 0; j < nrow && ok; ++j) {
-      const float *aj = rows + j * P.crow_stride;
+    for (int j = 0; j < nrow; ++j) {
+      const float *aj = rows + j * cs;
       float v = 0.f;
-      for (int c = 0; c < n; ++c) v = fmaf(aj[c], z[c], v);
-      const float bj = aj[P.crow_stride - 1];
-      ok = v <= bj + 1e-5f * fmaxf(1.f, fabsf(bj));
+#pragma unroll
+      for (int c = 0; c < N; ++c) v = fmaf(aj[c], z[c], v);
+      const float bj = aj[cs - 1];
+      if (v > bj + 1e-5f * fmaxf(1.f, fabsf(bj))) ok = false;
     }
     if (!ok) continue;
+    const int k = r == 0 ? 0 : (int)(P.rg_desc[base + r] & 15u);
+    bool dual = true;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      if (j < k) {
+        const float lj = __ldcg(tb + 2 * N * N + N + j);
+        float mu = lj, mag = fabsf(lj);
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+          const float t = __ldcg(tb + N * N + N + j * N + c) * w[c];
+          mu += t;
+          mag += fabsf(t);
+        }
+        if (mu < -1e-5f * mag) dual = false;
+      }
+    }
+    if (dual) {
+#pragma unroll
+      for (int a = 0; a < N; ++a) z_out[a] = z[a];
+      return;
+    }
     float obj = 0.f;
-    for (int a = 0; a < n; ++a) {
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
       float hz = cd * z[a];
-      for (int c = 0; c < n; ++c) hz = fmaf(C[a * n + c], z[c], hz);
+#pragma unroll
+      for (int c = 0; c < N; ++c) hz = fmaf(C[a * N + c], z[c], hz);
       obj = fmaf(z[a], 0.5f * hz - cd * w[a], obj);
     }
     if (obj < best) {
       best = obj;
 #pragma unroll
-      for (int a = 0; a < kMaxQP; ++a)
-        if (a < n) z_out[a] = z[a];
+      for (int a = 0; a < N; ++a) z_out[a] = z[a];
     }
+  }
+}
+
+// One slot of the block Phi-step: its N rows start at reduced position p0 and
+// hold w (from the row pass) in alpha; the slot QP gives z, and alpha becomes
+// (z - w)/s per row (0 when s = 0); own slot-0 inputs also give u(tau).
+template <int N>
+__device__ __forceinline__ void slot_solve(const Params &P, int key, bool slot0, int p0, int dred, const float *rec,
+                                           const float *C, const float *rt, float *alpha, float rho) {
+  float w[N], lo[N], hi[N], z[N];
+  int aux[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    const int p = p0 + a;
+    w[a] = alpha[p];
+    aux[a] = reinterpret_cast<const int *>(rt + p * kRowRecord)[3];
+    lo[a] = rt[p * kRowRecord + 5];
+    hi[a] = rt[p * kRowRecord + 6];
+    z[a] = w[a];
+  }
+  const float inv_s = rec[2];
+  if (inv_s > 0.f) {
+    if (P.expl)
+      slot_explicit<N>(P, key, slot0, C, rho * inv_s, w, z);
+    else
+      slot_box_qp<N>(C, rho * inv_s, w, lo, hi, z);
+  }
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    const int p = p0 + a;
+    alpha[p] = inv_s > 0.f ? (z[a] - w[a]) * inv_s : 0.f;
+    if (aux[a] >= 0 && p < dred) P.u[aux[a]] = z[a];
   }
 }
 
 // Phi-comp with full cost blocks Q_i, R_i: the rows of one member at one time
 // slot (its nx state rows or its nu input rows, consecutive in reduced order)
-// share x_hat and are solved together: w per row from the row sums, then
+// share x_hat and are solved together.  The row pass (phi_rows with W_ONLY)
+// has left w per row in alpha; here one thread per slot solves
 // min z^T C z + rho/(2 s) ||z - w||^2 over the slot's box (slot_box_qp with
 // H = 2 C + (rho/s) I) or, with coupled rows, over the slot's polytope
-// (slot_explicit), alpha = (z - w)/s per row.  One thread per slot.
+// (slot_explicit), and alpha = (z - w)/s per row.
 template <int NX>
-__device__ void phi_slots(const Params &P, const Item &it, const float *tab, const float *rt, const float *Gcur,
-                          float *alpha_out, float rho, int gt, int GT) {
-  const int T = it.T, r_sub = it.r_sub, rs_red = r_sub - NX, dred = it.dred, nu = P.nu;
+__device__ void phi_slots(const Params &P, const Item &it, const float *tab, const float *rt, float *alpha,
+                          float rho, int gt, int GT) {
+  const int T = it.T, rs_red = it.r_sub - NX, dred = it.dred, nu = P.nu;
   const int MT = member_record(NX, nu);
-  const int per = 2 * T - 1;  // T state slots, T - 1 input slots per member
-  for (int g = gt; g < it.n_mem * per; g += GT) {
-    const int mpos = small_div(g, per), kk = g - mpos * per;
-    int p0, n;
+  // the state slots of every member first, then the input slots: the costly
+  // state slots share the first round over the group's threads
+  const int nst = it.n_mem * T;
+  for (int g = gt; g < it.n_mem * (2 * T - 1); g += GT) {
+    int mpos, kk;
+    if (g < nst) {
+      mpos = small_div(g, T);
+      kk = g - mpos * T;
+    } else {
+      mpos = small_div(g - nst, T - 1);
+      kk = T + (g - nst - mpos * (T - 1));
+    }
     const float *rec = tab + mpos * MT;
     const float *C = rec + 4 + 4 * NX + 3 * nu;
+    const int key = P.expl ? 2 * P.members[it.mem_off + mpos] : 0;
     if (kk < T) {
-      n = NX;
-      p0 = kk == 0 ? dred + mpos * NX : mpos * rs_red + (kk - 1) * NX;
+      const int p0 = kk == 0 ? dred + mpos * NX : mpos * rs_red + (kk - 1) * NX;
+      slot_solve<NX>(P, key, kk == 0, p0, dred, rec, C, rt, alpha, rho);
     } else {
-      n = nu;
-      p0 = mpos * rs_red + (T - 1) * NX + (kk - T) * nu;
+      const int p0 = mpos * rs_red + (T - 1) * NX + (kk - T) * nu;
       C += NX * NX;
-    }
-    float w[kMaxQP], lo[kMaxQP], hi[kMaxQP], z[kMaxQP];
-    int aux[kMaxQP];
-#pragma unroll
-    for (int a = 0; a < kMaxQP; ++a) {
-      w[a] = 0.f;
-      lo[a] = -INFINITY;
-      hi[a] = INFINITY;
-      aux[a] = -1;
-      if (a < n) {
-        const int p = p0 + a;
-        const int4 ia = *reinterpret_cast<const int4 *>(rt + p * kRowRecord);
-        const float4 ca = *reinterpret_cast<const float4 *>(rt + p * kRowRecord + 4);
-        float s = 0.f;
-        for (int j = 0; j < ia.y; ++j) s += __ldcg(Gcur + ia.x + j * r_sub);
-        w[a] = s;
-        lo[a] = ca.y;
-        hi[a] = ca.z;
-        aux[a] = ia.w;
-      }
-      z[a] = w[a];
-    }
-    const float inv_s = rec[2];
-    if (inv_s > 0.f) {
-      if (P.expl)
-        slot_explicit(P, 2 * P.members[it.mem_off + mpos] + (kk < T ? 0 : 1), kk == 0, C, rho * inv_s, w, n, z);
-      else
-        slot_box_qp(C, rho * inv_s, w, lo, hi, n, z);
-    }
-#pragma unroll
-    for (int a = 0; a < kMaxQP; ++a) {
-      if (a < n) {
-        const int p = p0 + a;
-        alpha_out[p] = inv_s > 0.f ? (z[a] - w[a]) * inv_s : 0.f;
-        if (aux[a] >= 0 && p < dred) P.u[aux[a]] = z[a];
+      switch (nu) {
+        case 1: slot_solve<1>(P, key + 1, false, p0, dred, rec, C, rt, alpha, rho); break;
+        case 2: slot_solve<2>(P, key + 1, false, p0, dred, rec, C, rt, alpha, rho); break;
+        case 3: slot_solve<3>(P, key + 1, false, p0, dred, rec, C, rt, alpha, rho); break;
+        default: slot_solve<4>(P, key + 1, false, p0, dred, rec, C, rt, alpha, rho); break;
       }
     }
   }
@@ -1064,7 +1132,18 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
       if (P.expl && s_own > 0.f) {
         const float cd = P.rho_i[it.inst] * (1.f / s_own);
         const int nrx = P.rg_cnt[2 * it.sub], nr = nrx + P.rg_cnt[2 * it.sub + 1];
-        for (int e = gt; e < nr; e += GT) build_region(P, it.sub, e < nrx ? 0 : 1, e < nrx ? e : e - nrx, cd);
+        for (int e = gt; e < nr; e += GT) {
+          if (e < nrx) {
+            build_region<NX>(P, it.sub, 0, e, cd);
+          } else {
+            switch (P.nu) {
+              case 1: build_region<1>(P, it.sub, 1, e - nrx, cd); break;
+              case 2: build_region<2>(P, it.sub, 1, e - nrx, cd); break;
+              case 3: build_region<3>(P, it.sub, 1, e - nrx, cd); break;
+              default: build_region<4>(P, it.sub, 1, e - nrx, cd); break;
+            }
+          }
+        }
       }
     }
     float xj[NX];
@@ -1126,11 +1205,16 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
       for (int wi = 0; wi < wn; ++wi) {
         const Item &it = cached_item(G.icache, wi);
         if (!lact[it.lslot]) continue;
-        if constexpr (BLK)
-          phi_slots<NX>(P, it, G.mtab + wi * P.max_nmem * MT, G.rtab + wi * P.max_dcol * kRowRecord, Gcur,
+        phi_rows<GT, BLK>(P, it, G.rtab + wi * P.max_dcol * kRowRecord, Gcur, G.alpha + wi * P.max_dcol, gt);
+      }
+      if constexpr (BLK) {
+        group_sync(g, GT);  // every row's w is in alpha
+        for (int wi = 0; wi < wn; ++wi) {
+          const Item &it = cached_item(G.icache, wi);
+          if (!lact[it.lslot]) continue;
+          phi_slots<NX>(P, it, G.mtab + wi * P.max_nmem * MT, G.rtab + wi * P.max_dcol * kRowRecord,
                         G.alpha + wi * P.max_dcol, cached_extra(G.icache, wi)[0], gt, GT);
-        else
-          phi_rows<GT>(P, it, G.rtab + wi * P.max_dcol * kRowRecord, Gcur, G.alpha + wi * P.max_dcol, gt);
+        }
       }
       group_sync(g, GT);
       if (w0 == gi0) trace_point(P, iter, 1);

@@ -2,7 +2,7 @@
 profilers (ncu) and phase traces.
 
     python -m paper_2103_14990_gb300.profile_step --workload chain1024 \
-        --iters 50 --shape 1280701 --residency 2 --steps 3 [--trace]
+        --iters 50 --shape 1280701 --residency 2 --steps 3 [--trace] [--inner-qp coupled]
 
 --shape is threads per group * 10000 + groups per CTA * 100 + wave (0 keeps
 the default plan); --iters runs exactly that many ADMM iterations per step
@@ -27,12 +27,18 @@ def main(argv=None) -> int:
     ap.add_argument("--compact", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--trace", action="store_true")
+    ap.add_argument("--inner-qp", default="box", choices=["box", "block", "coupled"],
+                    help="block: full SPD cost blocks; coupled: also 2 coupled state rows per slot")
     a = ap.parse_args(argv)
     import torch
     import paper_2103_14990_gb300 as pkg
     from paper_2103_14990_gb300 import instances as I
     probs = I.batch256() if a.workload == "batch256" else \
         [{"chain1024": I.chain1024, "chain10": I.chain10, "grid64": I.grid64}[a.workload]()]
+    if a.inner_qp == "block":
+        probs = [I.with_block_costs(q, seed=101) for q in probs]
+    elif a.inner_qp == "coupled":
+        probs = [I.with_coupled_constraints(q, seed=102, n_cx=2, n_cu=0, g_range=(0.8, 1.2)) for q in probs]
     p = probs[0]
     s = pkg.Solver(probs)
     if a.residency >= 0:
