@@ -294,6 +294,7 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.inner_qp == "box":
         out["cpu_baseline"] = cpu_baseline(args, iters)
+        out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args, iters)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -414,6 +415,34 @@ def cpu_baseline(args, gpu_iters):
             "sample": f"{s['iters']} FP64 oracle ADMM iterations from x(0) ({s['t_iter'] * 1e3:.1f} ms each, "
                       f"one thread), scaled by {src} over the {len(its)} timed steps; one-time precompute excluded",
             "oracle_admm_iters_per_s": round(1.0 / s["t_iter"], 3)}
+
+
+def cpu_baseline_all_cores(args, gpu_iters, cores=None):
+    """The oracle on every host core: one single-threaded oracle process per
+    core, all timing the same bounded sample at once (the oracle's loops are
+    serial numpy, so the host's cores are used by independent copies)."""
+    cores = cores or min(os.cpu_count() or 1, 64)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload", args.workload,
+           "--sample-seconds", str(args.sample_seconds)]
+    procs = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                              env=_single_thread_env()) for _ in range(cores)]
+    rates, tails = [], []
+    for pr in procs:
+        out, err = pr.communicate(timeout=900)
+        if pr.returncode != 0:
+            return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": "failed: " + err[-300:]}
+        r = json.loads(out.strip().splitlines()[-1])
+        rates.append(1.0 / r["t_iter"])
+        tails.append(r["t_tail"])
+    table = oracle_iters_table(args.workload)
+    its = table["previous"]["iters"][:args.steps] if table is not None else gpu_iters
+    agg = sum(rates)                       # oracle ADMM iterations per second over all cores
+    t = sum(i / agg + max(tails) / cores for i in its)
+    return {"value": round(len(its) / t, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} single-threaded oracle processes at once, each timing FP64 ADMM iterations from "
+                      f"x(0) for {args.sample_seconds:g} s; aggregate {agg:.1f} iterations/s scaled by the same "
+                      f"per-step iteration counts as cpu_baseline",
+            "oracle_admm_iters_per_s": round(agg, 3)}
 
 
 def run_oracle_sample(args):

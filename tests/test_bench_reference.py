@@ -26,3 +26,17 @@ def test_reference_arm_json_line():
     from paper_2103_14990_gb300 import instances as I
     assert d["config"] == bench.bench_config(I.chain1024(), 1)
     assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+
+
+def test_all_cores_baseline_aggregates_processes():
+    """The all-cores oracle baseline runs one single-threaded oracle process
+    per core on the same bounded sample and adds their rates."""
+    import types
+    import bench
+    args = types.SimpleNamespace(workload="chain10", sample_seconds=0.2, steps=4)
+    out = bench.cpu_baseline_all_cores(args, [10, 10, 10, 10], cores=2)
+    assert out["cores"] == 2 and out["kind"] == "oracle"
+    assert out["value"] is not None and out["value"] > 0
+    assert out["oracle_admm_iters_per_s"] > 0
+    # four steps of ten iterations at the aggregate rate (plus the u/dynamics tail)
+    assert out["value"] <= 4 / (40 / out["oracle_admm_iters_per_s"]) + 1e-9
