@@ -223,7 +223,7 @@ def test_max_iter_status(torch):
 
 
 SHAPES = [(128, 4, 2, 2), (128, 4, 1, 0), (64, 4, 3, 1), (256, 2, 2, 0), (128, 1, 1, 2), (64, 2, 4, 0),
-          (64, 15, 1, 1), (96, 5, 1, 2), (96, 3, 2, 0), (128, 4, 1, 3), (256, 2, 1, 3), (64, 15, 1, 3),
+          (64, 15, 1, 1), (96, 5, 1, 2), (96, 3, 2, 0), (128, 4, 1, 3), (256, 2, 1, 3), (64, 4, 1, 3),
           (96, 3, 1, 3)]
 
 
