@@ -1614,15 +1614,26 @@ extern "C" int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value) {
     case DLMPC_OPT_BLOCK_PHI: ctx->force_block = value != 0; return 0;
     case DLMPC_OPT_RESIDENCY: {
       if (!(value >= 0 && value <= 3)) return ctx->fail(DLMPC_ERR_ARG, "residency must be 0, 1, 2 or 3");
+      const int old = ctx->residency;
       ctx->residency = (int)value;
       if (!ctx->precomputed) return 0;
-      return plan_sweep(ctx, ctx->gt, ctx->ng, ctx->wave, true);
+      const int rc = plan_sweep(ctx, ctx->gt, ctx->ng, ctx->wave, true);
+      if (rc == 0) return 0;
+      const std::string why = ctx->err;  // keep the previous plan
+      ctx->residency = old;
+      plan_sweep(ctx, ctx->gt, ctx->ng, ctx->wave, true);
+      return ctx->fail(rc, why);
     }
     case DLMPC_OPT_SWEEP_SHAPE: {
       // value = gt * 10000 + ng * 100 + wave
       const int v = (int)value;
       if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "set the sweep shape after dlmpc_precompute");
-      return plan_sweep(ctx, v / 10000, (v / 100) % 100, v % 100, true);
+      const int ogt = ctx->gt, ong = ctx->ng, owave = ctx->wave;
+      const int rc = plan_sweep(ctx, v / 10000, (v / 100) % 100, v % 100, true);
+      if (rc == 0) return 0;
+      const std::string why = ctx->err;  // keep the previous plan
+      plan_sweep(ctx, ogt, ong, owave, true);
+      return ctx->fail(rc, why);
     }
   }
   return ctx->fail(DLMPC_ERR_ARG, "unknown option");

@@ -41,10 +41,10 @@ def main(argv=None) -> int:
         probs = [I.with_coupled_constraints(q, seed=102, n_cx=2, n_cu=0, g_range=(0.8, 1.2)) for q in probs]
     p = probs[0]
     s = pkg.Solver(probs)
-    if a.residency >= 0:
-        s.set_option(pkg.OPT_RESIDENCY, a.residency)
     if a.shape > 0:
         s.set_option(pkg.OPT_SWEEP_SHAPE, a.shape)
+    if a.residency >= 0:
+        s.set_option(pkg.OPT_RESIDENCY, a.residency)
     s.set_option(pkg.OPT_COMPACT, a.compact)
     s.set_option(pkg.OPT_FIXED_ITERS, a.iters)
     s.set_option(pkg.OPT_TIMING, 1)

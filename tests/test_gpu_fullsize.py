@@ -164,8 +164,8 @@ def test_grid64_staged_operators_match_full_form():
     import paper_2103_14990_gb300 as pkg
     p = I.grid64()
     s = pkg.Solver([p])
-    s.set_option(pkg.OPT_RESIDENCY, 3)
     s.set_option(pkg.OPT_SWEEP_SHAPE, 2560201)
+    s.set_option(pkg.OPT_RESIDENCY, 3)
     info = s.info()
     assert info["resident_n_items"] == 0 and info["group_threads"] == 256 and info["wave"] == 1
     _compact_matches_full(s, [p], torch)

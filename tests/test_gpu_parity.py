@@ -241,8 +241,8 @@ def test_sweep_shapes_and_streaming(name, shape, torch):
     K = 23
     ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=K)
     s = gpu_solver([p], torch)
-    s.set_option(pkg.OPT_RESIDENCY, res)
     s.set_option(pkg.OPT_SWEEP_SHAPE, gt * 10000 + ng * 100 + wave)
+    s.set_option(pkg.OPT_RESIDENCY, res)
     info = s.info()
     assert info["group_threads"] == gt and info["groups_per_cta"] == ng and info["wave"] == wave
     if res == 0:
@@ -397,6 +397,28 @@ def test_block_phi_on_diagonal_costs_matches_row_phi(name, torch):
     _, _, phi_b, psi_b, _, u_b, _ = run_fixed(s, torch, p.x0, 30)
     assert rel(phi_b, phi_a) <= 1e-5 and rel(psi_b, psi_a) <= 1e-5
     assert rel(u_b, u_a) <= 1e-5 or np.max(np.abs(u_a - u_b)) < 1e-7
+    s.close()
+
+
+def test_failed_replan_keeps_the_previous_plan(torch):
+    """A residency or shape the kernel cannot take is refused and the
+    previous plan stays in force (the step still matches the oracle)."""
+    import paper_2103_14990_gb300 as pkg
+    p = SMALL["chain16_T10_d3_box"]()
+    s = gpu_solver([p], torch)
+    s.set_option(pkg.OPT_SWEEP_SHAPE, 1280402)
+    before = s.info()
+    with pytest.raises(pkg.DlmpcError):
+        s.set_option(pkg.OPT_RESIDENCY, 3)                 # staged N needs wave 1
+    with pytest.raises(pkg.DlmpcError):
+        s.set_option(pkg.OPT_SWEEP_SHAPE, 1280409)         # wave 9 is out of range
+    after = s.info()
+    for key in ("group_threads", "groups_per_cta", "wave", "resident_n_items", "smem_bytes"):
+        assert after[key] == before[key], key
+    o = O.Oracle(p)
+    ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=9)
+    _, _, phi, psi, _, _, _ = run_fixed(s, torch, p.x0, 9)
+    assert rel(psi, ref.Psi) <= REL
     s.close()
 
 
