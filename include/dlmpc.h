@@ -149,9 +149,7 @@ typedef struct {
                                           DLMPC_ERR_TIMEOUT (-1 = off, the default) */
 #define DLMPC_OPT_RESIDENCY 8     /* shared-memory residency during a step: 0 none (all streamed),
                                      1 compact iterate, Psi/Lambda and q, 2 (default) also N where
-                                     it fits, 3 as 1 and every patch's N is brought into a
-                                     per-group stage by one bulk copy per iteration, overlapped with
-                                     its Phi-step, and read there twice (needs wave 1); replans */
+                                     it fits; replans */
 #define DLMPC_OPT_BLOCK_PHI 14    /* != 0: use the slot box-QP Phi-step even when every cost
                                      block is diagonal (it is used whenever one is not) */
 #define DLMPC_OPT_COMPACT 13      /* != 0 (default): iterations after the first of a step carry the

@@ -27,8 +27,7 @@ cudaError_t launch_factor(const FactorParams &p, int grid, size_t smem, cudaStre
 cudaError_t launch_repack(const Item *scratch_items, const Item *items, int n_items, const float *src, float *dst,
                           cudaStream_t s);
 const void *sweep_kernel_ptr(int nx, int gt, bool blk);
-int sweep_group_floats(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad, int max_kpad, int max_nmem,
-                       int stage);
+int sweep_group_floats(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad, int max_kpad, int max_nmem);
 cudaStream_t mlp_stream(const dlmpc_mlp *mlp);
 cudaError_t launch_sweep(const Params &P, int gt, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_stats(const int32_t *inst_item_ptr, int n_inst, const float *item_r, const float *item_s,
@@ -145,10 +144,8 @@ struct dlmpc_ctx {
   int grid = 0, gt = 128, ng = 4, wave = 2, grp_floats = 0, cta_floats = 0, max_local_inst = 1;
   size_t smem = 0;
   int64_t resident_n_items = 0, resident_state_items = 0;
-  int residency = 2;  // 0: nothing resident, 1: compact iterate, Psi/Lambda and q resident, 2: also N,
-                      // 3: as 1, and each group stages every patch's N once per iteration
+  int residency = 2;  // 0: nothing resident, 1: compact iterate, Psi/Lambda and q resident, 2: also N
   int compact = 1;    // iterations after the first of a launch on the compact iterate
-  int stage_floats = 0;  // residency 3: floats of each group's stage
   bool block_cost = false;  // some instance has full cost blocks: slot box-QP Phi-step
   // Explicit solution of the slot QP with coupled rows (some instance has any):
   // per key 2 * global subsystem + kind (0 state, 1 input) the first region and
@@ -821,8 +818,6 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
   if (!(gt == 64 || gt == 96 || gt == 128 || gt == 256) || ng < 1 || ng > 15 || gt * ng > 1024 || wave < 1 || wave > 8)
     return ctx->fail(DLMPC_ERR_ARG, "unsupported sweep shape");
   if (ctx->max_kpad > 4 * gt) return ctx->fail(DLMPC_ERR_ARG, "null-space dimension too large for this group size");
-  if (ctx->residency >= 3 && wave != 1)
-    return ctx->fail(DLMPC_ERR_ARG, "staged N (residency 3) needs a Phi-step wave of 1");
   const int nx = ctx->nx;
   int dev = 0, sms = 0, smem_optin = 0;
   CK(cudaGetDevice(&dev), "cudaGetDevice");
@@ -859,25 +854,8 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
   int64_t used_max = 0;
   std::vector<std::vector<std::vector<int32_t>>> groups(grid);
   for (int pass = 0; pass < 2; ++pass) {
-    // residency 3: a stage per group for the largest N that fits beside the
-    // group buffers and the per-CTA counters (larger patches read global memory)
-    int stage = 0;
-    if (ctx->residency >= 3) {
-      const int grp0 = sweep_group_floats(nx, ctx->nu, gt, wave, ctx->max_dcol, ctx->max_dred_pad, ctx->max_kpad,
-                                          ctx->max_nmem, 0);
-      const int64_t room = (budget - (int64_t)ng * grp0 - cta_floats) / ng;
-      int64_t best = 0, smallest = INT64_MAX;
-      for (const Item &it : ctx->items) {
-        const int64_t nf = (int64_t)it.dred_pad * it.kpad;
-        smallest = std::min(smallest, nf);
-        if (nf <= room) best = std::max(best, nf);
-      }
-      if (best == 0 || best < smallest) return ctx->fail(DLMPC_ERR_ARG, "no patch's N fits a stage with this shape");
-      stage = (int)best;
-    }
-    ctx->stage_floats = stage;
     const int grp = sweep_group_floats(nx, ctx->nu, gt, wave, ctx->max_dcol, ctx->max_dred_pad, ctx->max_kpad,
-                                       ctx->max_nmem, stage);
+                                       ctx->max_nmem);
     const int64_t arena_cap = budget - (int64_t)ng * grp - cta_floats;
     if (arena_cap < 0) return ctx->fail(DLMPC_ERR_ARG, "shared-memory budget exceeded by the group buffers");
     used_max = 0;
@@ -909,7 +887,7 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
       for (int id : rr) {
         Item &it = ctx->items[id];
         const int64_t need = (int64_t)it.dred_pad * it.kpad;  // N only: resident patches skip N^T
-        if (ctx->residency == 2 && used + need <= arena_cap) {
+        if (ctx->residency >= 2 && used + need <= arena_cap) {
           it.n_sm = (int32_t)used;
           used += need;
           ++ctx->resident_n_items;
@@ -1302,8 +1280,6 @@ Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_d
   P.trace = ctx->trace ? ctx->d_trace.p : nullptr;
   P.skip_arrival_cta = ctx->skip_arrival_cta;
   P.compact = ctx->compact;
-  P.stream = ctx->residency >= 3 ? 1 : 0;
-  P.stage_floats = ctx->stage_floats;
   P.block_cost = (ctx->block_cost || ctx->force_block) ? 1 : 0;
   P.qblk2 = ctx->d_qblk2.p;
   P.rblk2 = ctx->d_rblk2.p;
@@ -1537,7 +1513,7 @@ extern "C" int dlmpc_autotune(dlmpc_ctx *ctx, const float *x_dev, int32_t iters,
   static const int kGt[] = {64, 96, 128, 256};
   static const int kNg[] = {1, 2, 4, 6, 8, 12, 15};
   static const int kWave[] = {1, 2};
-  static const int kRes[] = {2, 1, 3};
+  static const int kRes[] = {2, 1};
   std::vector<std::tuple<int, int, int, int, int>> seen;
   for (int res : kRes)
     for (int gt : kGt)
@@ -1613,7 +1589,7 @@ extern "C" int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value) {
     case DLMPC_OPT_COMPACT: ctx->compact = value != 0; return 0;
     case DLMPC_OPT_BLOCK_PHI: ctx->force_block = value != 0; return 0;
     case DLMPC_OPT_RESIDENCY: {
-      if (!(value >= 0 && value <= 3)) return ctx->fail(DLMPC_ERR_ARG, "residency must be 0, 1, 2 or 3");
+      if (!(value >= 0 && value <= 2)) return ctx->fail(DLMPC_ERR_ARG, "residency must be 0, 1 or 2");
       const int old = ctx->residency;
       ctx->residency = (int)value;
       if (!ctx->precomputed) return 0;

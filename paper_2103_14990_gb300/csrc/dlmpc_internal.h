@@ -108,9 +108,6 @@ struct Params {
   int32_t skip_arrival_cta;   // test of the bounded waits: this CTA leaves before its first
                               // iteration barrier (-1 = none)
   int32_t compact;            // != 0: iterations after the first use the compact iterate
-  int32_t stream;             // != 0 (wave 1): N of a patch is sent to the group's stage by one
-                              // bulk copy per iteration and read there twice ...
-  int32_t stage_floats;       // ... when dred_pad * kpad fits this stage (others read global memory)
   int32_t block_cost;         // != 0: Phi-step by slot box-QP with the full cost blocks
   const float *qblk2, *rblk2; // [sub][nx][nx] 2 Q_i, [sub][nu][nu] 2 R_i
   // explicit solution of the slot QP with coupled rows (null: boxes only);

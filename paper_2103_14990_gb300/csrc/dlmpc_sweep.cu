@@ -35,7 +35,7 @@
 namespace dlmpc {
 
 struct GroupLayout {
-  int alpha, vred, psired, t, part, red, mtab, rtab, icache, mbar, stage, total;
+  int alpha, vred, psired, t, part, red, mtab, rtab, icache, mbar, total;
 };
 
 // Floats of one cached item: the Item, then rho, eps_p, eps_d, its own index.
@@ -58,9 +58,8 @@ constexpr int kRowRecord = 8;
 __host__ __device__ inline int member_record(int nx, int nu) { return 4 + 4 * nx + 3 * nu + nx * nx + nu * nu; }
 
 // Float offsets inside one group region; the host uses the same function.
-// stage: floats of the buffer that receives a streamed patch's N (0: none).
 __host__ __device__ inline GroupLayout group_layout(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad,
-                                                    int max_kpad, int max_nmem, int stage) {
+                                                    int max_kpad, int max_nmem) {
   GroupLayout L;
   int o = 0;
   L.alpha = o;  o += round4(wave * max_dcol);
@@ -73,7 +72,6 @@ __host__ __device__ inline GroupLayout group_layout(int nx, int nu, int gt, int 
   L.rtab = o;   o += wave * max_dcol * kRowRecord;
   L.icache = o; o += round4(wave * kItemFloats);
   L.mbar = o;   o += 4;
-  L.stage = o;  o += round4(stage);
   L.total = o;
   return L;
 }
@@ -90,7 +88,7 @@ __device__ __forceinline__ void group_sync(int g, int gt_threads) {
 }
 
 struct Group {
-  float *alpha, *vred, *psired, *t, *part, *mtab, *rtab, *icache, *stage;
+  float *alpha, *vred, *psired, *t, *part, *mtab, *rtab, *icache;
   double *red;
   uint64_t *mbar;
   unsigned phase;  // completed bulk copies on mbar
@@ -870,39 +868,10 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
 // 16-byte column group g of every QS-th row starting at row q, so a warp reads
 // consecutive 16-byte units, and the QS partial sums per output are added
 // afterwards.
-// A patch whose N is brought to its group's stage every iteration (residency
-// 3): not resident, and small enough for the stage.
-__device__ __forceinline__ bool staged_n(const Params &P, const Item &it) {
-  return P.stream && it.n_sm < 0 && it.dred_pad * it.kpad <= P.stage_floats;
-}
-
-// o = N y for a patch whose N (rows x ld, row-major) sits in shared memory:
-// one thread per row, whole 16-byte units, the unit order rotated by the row
-// so that the eight rows of a quarter warp fall on different banks.
-__device__ __forceinline__ void row_pass(const float *N, int rows, int ld, const float *y, float *out, int gt,
-                                         int GT) {
-  const int nu4 = ld >> 2;
-  for (int r = gt; r < rows; r += GT) {
-    const float4 *nr = reinterpret_cast<const float4 *>(N + (int64_t)r * ld);
-    const float4 *y4 = reinterpret_cast<const float4 *>(y);
-    int c = r % nu4;
-    float a0 = 0.f, a1 = 0.f;
-    for (int e = 0; e < nu4; ++e) {
-      const float4 m = nr[c], v = y4[c];
-      a0 = fmaf(m.x, v.x, a0);
-      a1 = fmaf(m.y, v.y, a1);
-      a0 = fmaf(m.z, v.z, a0);
-      a1 = fmaf(m.w, v.w, a1);
-      c = c + 1 == nu4 ? 0 : c + 1;
-    }
-    out[r] = a0 + a1;
-  }
-}
-
 template <int NX, int GT>
 __device__ void project_compact(const Params &P, int idx, const Item &it, const float *tab, const float *rt,
                                 const float *extra, Group &G, const float *alpha, float *arena, float *Gnext, int g,
-                                int gt, unsigned *lnc, int iter, bool first, bool tr, bool streamed) {
+                                int gt, unsigned *lnc, int iter, bool first, bool tr) {
   const int MT = member_record(NX, P.nu);
   const int r_sub = it.r_sub;
   const int dcol = r_sub * it.n_mem;
@@ -916,12 +885,6 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
   const float *lam_p = it.st_sm >= 0 ? arena + it.st_sm + NX * dcol : P.Lam + it.st_off;
   const float *Nb = it.n_sm >= 0 ? arena + it.n_sm : P.Nmat + it.n_off;
   const float *NTb = P.Nmat + it.n_off + dpad * kpad;  // N^T (k x dred_pad) follows N in global memory
-  if (streamed) {  // this patch's N was sent to the group's stage before its Phi-step
-    const bool arrived = mbar_wait(G.mbar, G.phase & 1u, P.timeout_ns);
-    ++G.phase;
-    if (!arrived && gt == 0) set_error(P.err, DLMPC_ERR_TIMEOUT, blockIdx.x, iter, 3);
-    Nb = G.stage;
-  }
   float xj[NX];
   float s = 0.f;
 #pragma unroll
@@ -947,12 +910,8 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
   group_sync(g, GT);
   if (tr) trace_point(P, iter, 7);
 
-  // pass 2: o = N y, flat over N^T (from L2 also for patches whose N is
-  // resident), or by rows of the staged N (a streamed patch reads N once)
-  if (streamed)
-    row_pass(Nb, dred, kpad, G.t, G.part, gt, GT);
-  else
-    flat_pass<8>(NTb, k, dpad, G.t, G.part, gt, GT);
+  // pass 2: o = N y, flat over N^T (from L2 also for patches whose N is resident)
+  flat_pass<8>(NTb, k, dpad, G.t, G.part, gt, GT);
   group_sync(g, GT);
   if (tr) trace_point(P, iter, 6);
 
@@ -960,7 +919,7 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
   float prim_f = 0.f, dual_f = 0.f;
   {
     const int nrg = dpad >> 2;
-    const int QS = streamed ? 1 : (GT >= nrg ? small_div(GT, nrg) : 1);
+    const int QS = GT >= nrg ? small_div(GT, nrg) : 1;
     for (int red = gt; red < dred; red += GT) {
       float o = 0.f;
       for (int q = 0; q < QS; ++q) o += G.part[q * dpad + red];
@@ -1103,8 +1062,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
   const int tid = threadIdx.x;
   const int g = tid / GT, gt = tid - g * GT;
   const int b = blockIdx.x;
-  const GroupLayout L = group_layout(NX, P.nu, GT, P.wave, P.max_dcol, P.max_dred_pad, P.max_kpad, P.max_nmem,
-                                     P.stream ? P.stage_floats : 0);
+  const GroupLayout L = group_layout(NX, P.nu, GT, P.wave, P.max_dcol, P.max_dred_pad, P.max_kpad, P.max_nmem);
   float *gbase = sm + g * P.grp_floats;
   Group G;
   G.alpha = gbase + L.alpha;
@@ -1117,7 +1075,6 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
   G.rtab = gbase + L.rtab;
   G.icache = gbase + L.icache;
   G.mbar = reinterpret_cast<uint64_t *>(gbase + L.mbar);
-  G.stage = gbase + L.stage;
   G.phase = 0;
   float *cta = sm + P.ng * P.grp_floats;
   unsigned long long *prev_hi = reinterpret_cast<unsigned long long *>(cta);  // [3] (+1 pad)
@@ -1248,9 +1205,6 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
       for (int wi = 0; wi < wn; ++wi) {
         const Item &it = cached_item(G.icache, wi);
         if (!lact[it.lslot]) continue;
-        // streamed N: one bulk copy to the group's stage, in flight during the Phi-step (wave 1)
-        if (compact && iter > 0 && gt == 0 && staged_n(P, it))
-          tma_load_1d(G.stage, P.Nmat + it.n_off, (unsigned)it.dred_pad * it.kpad * 4u, G.mbar);
         phi_rows<GT, BLK>(P, it, G.rtab + wi * P.max_dcol * kRowRecord, Gcur, G.alpha + wi * P.max_dcol, gt);
       }
       if constexpr (BLK) {
@@ -1273,7 +1227,7 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
         if (compact && iter > 0)
           project_compact<NX, GT>(P, idx, it, G.mtab + wi * P.max_nmem * MT, G.rtab + wi * P.max_dcol * kRowRecord,
                                   ex, G, G.alpha + wi * P.max_dcol, arena,
-                                  Gnext, g, gt, lnc, iter, iter == 1, tr, staged_n(P, it));
+                                  Gnext, g, gt, lnc, iter, iter == 1, tr);
         else
           project_item<NX, GT>(P, idx, it, G.mtab + wi * P.max_nmem * MT, ex, G, G.alpha + wi * P.max_dcol, arena,
                                Gnext, g, gt, lnc, iter,
@@ -1383,9 +1337,8 @@ const void *sweep_kernel_ptr(int nx, int gt, bool blk) {
   return nullptr;
 }
 
-int sweep_group_floats(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad, int max_kpad, int max_nmem,
-                       int stage) {
-  return group_layout(nx, nu, gt, wave, max_dcol, max_dred_pad, max_kpad, max_nmem, stage).total;
+int sweep_group_floats(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad, int max_kpad, int max_nmem) {
+  return group_layout(nx, nu, gt, wave, max_dcol, max_dred_pad, max_kpad, max_nmem).total;
 }
 
 cudaError_t launch_sweep(const Params &P, int gt, int grid, size_t smem, cudaStream_t s) {

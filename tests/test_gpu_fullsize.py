@@ -154,19 +154,3 @@ def test_batch256_sampled_iteration():
     _one_iteration_check(s, probs, lambda b, q: ([0, q.n_sub // 2, q.n_sub - 1] if b in picked else []), torch)
     _compact_matches_full(s, probs, torch)
     s.close()
-
-
-def test_grid64_staged_operators_match_full_form():
-    """Residency 3 on the 64x64 grid: every patch's N goes to its group's
-    stage by one bulk copy per iteration and both passes read it there; the
-    compact iterate on that plan against the full form."""
-    import torch
-    import paper_2103_14990_gb300 as pkg
-    p = I.grid64()
-    s = pkg.Solver([p])
-    s.set_option(pkg.OPT_SWEEP_SHAPE, 2560201)
-    s.set_option(pkg.OPT_RESIDENCY, 3)
-    info = s.info()
-    assert info["resident_n_items"] == 0 and info["group_threads"] == 256 and info["wave"] == 1
-    _compact_matches_full(s, [p], torch)
-    s.close()
