@@ -19,6 +19,9 @@ Pinned parts (see tests/test_oracle_pins.py):
                     centralised QP with coupled rows (KKT at the ADMM solution);
   * psi projector - Z psi = e exactly, idempotent symmetric projector, min-norm offset
                     against lstsq, residual orthogonal to the null space;
+  * admm(stale=) - p = 0 is the exchange-free admm; a per-message loop on
+                    small cases gives the same iterates; the loss draws are
+                    uniform and independent, at rate p; Z_AB Psi = I holds;
   * admm / mpc    - converged trajectory against the centralised
                     locality-constrained QP (least squares / SLSQP) and, for
                     d >= N-1 with no boxes, against the textbook finite-horizon
@@ -274,12 +277,16 @@ def phi_step_row(v: np.ndarray, xh: np.ndarray, qw: float, rho: float,
     return v + ((z - w) / s) * xh
 
 
-def phi_step(lay: Layout, Psi: np.ndarray, Lam: np.ndarray, x0: np.ndarray, rho: float):
-    """Row-wise Phi-comp for every row at once: returns (Phi, z) with z = Phi x0 per row."""
+def phi_step(lay: Layout, Psi: np.ndarray, Lam: np.ndarray, x0: np.ndarray, rho: float,
+             w: Optional[np.ndarray] = None):
+    """Row-wise Phi-comp for every row at once: returns (Phi, z) with z = Phi x0 per row.
+    `w` replaces the row sums (Psi - Lambda) x_hat when the rows see other
+    values than the current ones (stale messages, `admm(stale=...)`)."""
     xf = x0.reshape(-1)
     xe = xf[lay.cols]
     V = Psi - Lam
-    w = np.bincount(lay.rows, weights=V * xe, minlength=lay.n_rows)
+    if w is None:
+        w = np.bincount(lay.rows, weights=V * xe, minlength=lay.n_rows)
     s = np.bincount(lay.rows, weights=xe * xe, minlength=lay.n_rows)
     zstar = rho * w / (rho + 2.0 * lay.qw * s)
     z = np.minimum(np.maximum(zstar, lay.lo), lay.hi)
@@ -380,7 +387,8 @@ def slot_constraints(prob, i: int, kind: str, t: int):
     return (np.array(rows).reshape(-1, n), np.array(rhs))
 
 
-def phi_step_block(lay: Layout, Psi: np.ndarray, Lam: np.ndarray, x0: np.ndarray, rho: float):
+def phi_step_block(lay: Layout, Psi: np.ndarray, Lam: np.ndarray, x0: np.ndarray, rho: float,
+                   w: Optional[np.ndarray] = None):
     """Phi-comp with full cost blocks Q_i, R_i (Sec. II-A with non-diagonal
     Q_t, R_t): the rows of subsystem i at one time slot (its nx state rows, or
     its nu input rows) share x_hat_i, so with w = (Psi - Lambda) x_hat per row,
@@ -395,7 +403,8 @@ def phi_step_block(lay: Layout, Psi: np.ndarray, Lam: np.ndarray, x0: np.ndarray
     xf = x0.reshape(-1)
     xe = xf[lay.cols]
     V = Psi - Lam
-    w = np.bincount(lay.rows, weights=V * xe, minlength=lay.n_rows)
+    if w is None:
+        w = np.bincount(lay.rows, weights=V * xe, minlength=lay.n_rows)
     s = np.bincount(lay.rows, weights=xe * xe, minlength=lay.n_rows)
     Qb = prob.Q_blk if prob.Q_blk is not None else np.array([np.diag(q) for q in prob.q])
     Rb = prob.R_blk if prob.R_blk is not None else np.array([np.diag(r) for r in prob.r])
@@ -454,17 +463,82 @@ class AdmmResult:
     s_max: float
 
 
+# ----------------------------------------------------------------------------
+# Stale messages: the fully distributed setting (Sec. V), simulated
+# ----------------------------------------------------------------------------
+#
+# In the distributed setting every subsystem j tells each member m of its patch
+# the sums over j's columns of (Psi - Lambda)[row of m, c] x_c, one per row of
+# m (the column-patch exchange of Sec. III-D).  A message (j -> m) sent at the
+# end of iteration k is lost with probability p; the receiver then keeps the
+# last value it received from j (dropouts, and delays of one or more
+# iterations, look the same to it).  The draws come from the counter-based
+# SplitMix64 generator (Steele, Lea and Flood, 2014): draw n of seed S is the
+# generator's output after n + 1 steps, mix(S + (n + 1) gamma); message
+# (k, j, m) uses n = (k N + j) N + m and is lost when the top 53 bits of the
+# draw are below floor(p 2^53).
+
+_SM_GAMMA = 0x9E3779B97F4A7C15
+_SM_MUL1 = 0xBF58476D1CE4E5B9
+_SM_MUL2 = 0x94D049BB133111EB
+
+
+def splitmix64_at(seed: int, n):
+    """Output n (0-based) of SplitMix64 seeded with `seed`; n an int or an
+    array of non-negative integers (uint64 arithmetic, wrapping mod 2^64)."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (np.asarray(n, dtype=np.uint64) + np.uint64(1)) * np.uint64(_SM_GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(_SM_MUL1)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(_SM_MUL2)
+        return z ^ (z >> np.uint64(31))
+
+
+def stale_threshold(p: float) -> int:
+    """floor(p 2^53): a message is lost when (draw >> 11) < this."""
+    return int(p * 9007199254740992.0)
+
+
+def message_lost(seed: int, thr: int, k: int, j, m, n_sub: int):
+    n = (np.uint64(k) * np.uint64(n_sub) + np.asarray(j, np.uint64)) * np.uint64(n_sub) + np.asarray(m, np.uint64)
+    return (splitmix64_at(seed, n) >> np.uint64(11)) < np.uint64(thr)
+
+
+class Messages:
+    """The (row, sending subsystem) pairs of one layout: pair of every stored
+    entry, and the row, sender j and receiver m of every pair."""
+
+    def __init__(self, lay: Layout):
+        n = lay.prob.n_sub
+        key = lay.rows * n + lay.col_sub
+        uniq, first, self.pair_of_entry = np.unique(key, return_index=True, return_inverse=True)
+        self.row = uniq // n
+        self.j = uniq % n
+        self.m = lay.row_sub[first]          # row_sub is per stored entry
+        self.n_pairs = len(uniq)
+
+    def sums(self, lay: Layout, V: np.ndarray, x0: np.ndarray) -> np.ndarray:
+        """The message values: per pair, sum over the sender's columns of V x."""
+        xe = x0.reshape(-1)[lay.cols]
+        return np.bincount(self.pair_of_entry, weights=V * xe, minlength=self.n_pairs)
+
+    def row_sums(self, lay: Layout, D: np.ndarray) -> np.ndarray:
+        """w per row: the sum of the values the row's owner holds."""
+        return np.bincount(self.row, weights=D, minlength=lay.n_rows)
+
+
 def admm(lay: Layout, blocks: List[ColumnBlock], x0: np.ndarray, *,
          Psi0: Optional[np.ndarray] = None, Lam0: Optional[np.ndarray] = None,
          learned: Optional[tuple] = None, max_iter: Optional[int] = None,
          fixed_iters: Optional[int] = None, eps_p: Optional[float] = None,
-         eps_d: Optional[float] = None) -> AdmmResult:
+         eps_d: Optional[float] = None, stale: Optional[tuple] = None) -> AdmmResult:
     """Alg. 2: repeat Phi-comp, Psi-comp, Lambda-comp, Conv.
 
     Start: cold (Psi = Lambda = 0) unless Psi0/Lam0 are given.  `learned`
     = (Phi_init, Lam_init) replaces the first Phi-step: Psi0 = proj(Phi_init +
     Lam_init), Lam0 = Lam_init + Phi_init - Psi0.  `fixed_iters` runs exactly
-    that many iterations with Conv ignored."""
+    that many iterations with Conv ignored.  `stale` = (p, seed) simulates lost
+    messages (see Messages): the Phi-step's row sums are the values last
+    received, the start state's being received before the first iteration."""
     prob = lay.prob
     rho = prob.rho
     eps_p = prob.eps_p if eps_p is None else eps_p
@@ -483,10 +557,20 @@ def admm(lay: Layout, blocks: List[ColumnBlock], x0: np.ndarray, *,
     Phi = z = None
     block = (prob.Q_blk is not None or prob.R_blk is not None
              or prob.Gx is not None or prob.Gu is not None)
+    msg = held = None
+    if stale is not None:
+        msg = Messages(lay)
+        thr = stale_threshold(stale[0])
+        held = msg.sums(lay, Psi - Lam, x0)
     for it in range(1, n_it + 1):
-        Phi, z = (phi_step_block if block else phi_step)(lay, Psi, Lam, x0, rho)
+        w = msg.row_sums(lay, held) if msg is not None else None
+        Phi, z = (phi_step_block if block else phi_step)(lay, Psi, Lam, x0, rho, w=w)
         Psi_new = psi_step(lay, blocks, Phi + Lam)
         Lam = Lam + Phi - Psi_new
+        if msg is not None:
+            fresh = msg.sums(lay, Psi_new - Lam, x0)
+            lost = message_lost(int(stale[1]), thr, it - 1, msg.j, msg.m, prob.n_sub)
+            held = np.where(lost, held, fresh)
         r_max = float(np.max(per_subsystem_norm(lay, Phi - Psi_new)))
         s_max = float(rho * np.max(per_subsystem_norm(lay, Psi_new - Psi)))
         Psi = Psi_new

@@ -709,3 +709,104 @@ def test_planted_coupled_sign_flip_is_caught(monkeypatch):
     monkeypatch.setattr(O, "slot_constraints", flipped)
     with pytest.raises(AssertionError):
         test_coupled_admm_matches_centralised_qp()
+
+
+# --------------------------------------------------------------------------
+# Stale messages (the distributed setting simulated): admm(stale=(p, seed))
+# --------------------------------------------------------------------------
+
+def test_splitmix64_published_outputs():
+    """The first outputs of SplitMix64 seeded with 0, as its reference
+    implementation prints them."""
+    assert int(O.splitmix64_at(0, 0)) == 0xE220A8397B1DCDAF
+    assert int(O.splitmix64_at(0, 1)) == 0x6E789E6AA1B965F4
+    # vectorised draws equal the scalar ones
+    v = O.splitmix64_at(12345, np.arange(5))
+    assert [int(a) for a in v] == [int(O.splitmix64_at(12345, n)) for n in range(5)]
+
+
+def test_loss_draws_are_uniform_and_independent():
+    rng_n = 64
+    k = np.repeat(np.arange(200), rng_n * rng_n)
+    j = np.tile(np.repeat(np.arange(rng_n), rng_n), 200)
+    m = np.tile(np.arange(rng_n), 200 * rng_n)
+    for p in (0.1, 0.5):
+        lost = O.message_lost(7, O.stale_threshold(p), 0, j[:rng_n * rng_n], m[:rng_n * rng_n], rng_n)
+        n = lost.size
+        assert abs(lost.mean() - p) < 4 * np.sqrt(p * (1 - p) / n)
+    lost = np.concatenate([O.message_lost(7, O.stale_threshold(0.5), kk, j[:rng_n * rng_n], m[:rng_n * rng_n], rng_n)
+                           for kk in range(20)]).reshape(20, -1).astype(float)
+    c = np.corrcoef(lost[:-1].ravel(), lost[1:].ravel())[0, 1]          # iteration to iteration
+    assert abs(c) < 0.02
+    assert not O.message_lost(7, O.stale_threshold(0.0), 3, 1, 2, 8)
+    assert O.message_lost(7, O.stale_threshold(1.0), 3, 1, 2, 8)
+
+
+def test_stale_with_p0_is_plain_admm():
+    p = I.make_instance(12, 5, 2, seed=4, boxes=True, x0_dist="uniform")
+    o = O.Oracle(p)
+    a = O.admm(o.lay, o.blocks, p.x0, fixed_iters=30)
+    b = O.admm(o.lay, o.blocks, p.x0, fixed_iters=30, stale=(0.0, 9))
+    assert np.allclose(a.Psi, b.Psi, atol=1e-12) and np.allclose(a.Phi, b.Phi, atol=1e-12)
+    c = O.admm(o.lay, o.blocks, p.x0, fixed_iters=30, stale=(0.3, 9))
+    assert np.max(np.abs(c.Psi - a.Psi)) > 1e-6                           # losses change the iterates
+
+
+def _stale_admm_by_messages(p, K, prob_loss, seed):
+    """Per-message restatement on a tiny instance: every (sender j, receiver
+    m, local row r) value kept in a dict and updated by loops."""
+    o = O.Oracle(p)
+    lay = o.lay
+    xf = p.x0.reshape(-1)
+    thr = O.stale_threshold(prob_loss)
+
+    def sums(V):
+        out = {}
+        for e in range(lay.nnz):
+            key = (int(lay.col_sub[e]), int(lay.row_sub[e]), int(lay.row_local[e]))
+            out[key] = out.get(key, 0.0) + V[e] * xf[lay.cols[e]]
+        return out
+
+    Psi = np.zeros(lay.nnz)
+    Lam = np.zeros(lay.nnz)
+    held = sums(Psi - Lam)
+    for k in range(K):
+        w = np.zeros(lay.n_rows)
+        for (j, m, r), v in held.items():
+            w[O.global_row(p, m, r)] += v
+        Phi, _ = O.phi_step(lay, Psi, Lam, p.x0, p.rho, w=w)
+        Psi_new = O.psi_step(lay, o.blocks, Phi + Lam)
+        Lam = Lam + Phi - Psi_new
+        Psi = Psi_new
+        fresh = sums(Psi - Lam)
+        for (j, m, r) in held:
+            n = (k * p.n_sub + j) * p.n_sub + m                  # the message's draw number
+            if not (int(O.splitmix64_at(seed, n)) >> 11) < thr:
+                held[(j, m, r)] = fresh[(j, m, r)]
+    return Psi, Lam
+
+
+def test_stale_admm_matches_per_message_loops():
+    p = I.make_instance(5, 3, 1, seed=2, boxes=True, x0_dist="uniform")
+    o = O.Oracle(p)
+    ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=12, stale=(0.4, 77))
+    Psi, Lam = _stale_admm_by_messages(p, 12, 0.4, 77)
+    assert np.allclose(ref.Psi, Psi, atol=1e-12) and np.allclose(ref.Lam, Lam, atol=1e-12)
+
+
+def test_stale_admm_keeps_the_affine_constraint():
+    p = I.make_instance(8, 4, 2, seed=5, boxes=True, x0_dist="uniform")
+    o = O.Oracle(p)
+    res = O.admm(o.lay, o.blocks, p.x0, fixed_iters=25, stale=(0.5, 3))
+    Z = O.global_Z_AB(p)
+    Psi = o.lay.to_dense(res.Psi)
+    rhs = np.zeros((Z.shape[0], p.n_sub * p.nx)); rhs[:p.n_sub * p.nx] = np.eye(p.n_sub * p.nx)
+    assert np.max(np.abs(Z @ Psi - rhs)) < 1e-10
+
+
+def test_planted_wrong_receiver_is_caught(monkeypatch):
+    """Loss draws keyed on the wrong receiver fail the per-message check."""
+    real = O.message_lost
+    monkeypatch.setattr(O, "message_lost", lambda seed, thr, k, j, m, n: real(seed, thr, k, m, j, n))
+    with pytest.raises(AssertionError):
+        test_stale_admm_matches_per_message_loops()
