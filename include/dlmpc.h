@@ -152,6 +152,15 @@ typedef struct {
                                      it fits; replans */
 #define DLMPC_OPT_BLOCK_PHI 14    /* != 0: use the slot box-QP Phi-step even when every cost
                                      block is diagonal (it is used whenever one is not) */
+#define DLMPC_OPT_STALE_PROB 15   /* probability p in [0, 1] that a message is lost (default 0),
+                                     simulating the fully distributed setting (Sec. V): the row
+                                     sums patch j sends to member m at the end of iteration k are
+                                     lost when output n = (k N + j) N + m of SplitMix64 seeded with
+                                     DLMPC_OPT_STALE_SEED, shifted right by 11 bits, is below
+                                     floor(p 2^53) (N = subsystems of the context, j, m global
+                                     indices); the receiver keeps the last value it received (the
+                                     start state's before the first iteration) */
+#define DLMPC_OPT_STALE_SEED 16   /* seed of those draws (a non-negative integer, default 0) */
 #define DLMPC_OPT_COMPACT 13      /* != 0 (default): iterations after the first of a step carry the
                                      projected iterate as Psi = q + N t and Lambda = x_c lhat (the
                                      same iterates as Alg. 2, with the v = Psi + alpha x algebra of

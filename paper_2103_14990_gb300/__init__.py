@@ -44,6 +44,8 @@ OPT_LEARN_PLANT = 11
 OPT_TEST_SKIP_ARRIVAL = 12
 OPT_COMPACT = 13
 OPT_BLOCK_PHI = 14
+OPT_STALE_PROB = 15
+OPT_STALE_SEED = 16
 
 # Every entry point declared in include/dlmpc.h (checked by the tests).
 EXPORTED = [

@@ -157,6 +157,7 @@ struct dlmpc_ctx {
   std::vector<float> h_crow;  // rows: normal [nmax] then right-hand side
   int expl_stride = 0, crow_stride = 0;
   int force_block = 0;      // DLMPC_OPT_BLOCK_PHI
+  unsigned long long stale_thr = 0, stale_seed = 0;  // DLMPC_OPT_STALE_PROB (floor(p 2^53)), _SEED
   int trace = 0;
   std::vector<int32_t> grp_ptr, grp_items, cta_inst_ptr, cta_inst;
   // options
@@ -194,10 +195,11 @@ struct dlmpc_ctx {
     int plan, fixed, max_iter;
     bool phi, trace;
     int compact, block;
+    unsigned long long stale_thr, stale_seed;
     bool operator==(const GraphKey &o) const {
       return x == o.x && u == o.u && xn == o.xn && warm == o.warm && stats == o.stats && plan == o.plan &&
              fixed == o.fixed && max_iter == o.max_iter && phi == o.phi && trace == o.trace && compact == o.compact &&
-             block == o.block;
+             block == o.block && stale_thr == o.stale_thr && stale_seed == o.stale_seed;
     }
   };
   struct GraphEntry {
@@ -1280,6 +1282,8 @@ Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_d
   P.trace = ctx->trace ? ctx->d_trace.p : nullptr;
   P.skip_arrival_cta = ctx->skip_arrival_cta;
   P.compact = ctx->compact;
+  P.stale_thr = ctx->stale_thr;
+  P.stale_seed = ctx->stale_seed;
   P.block_cost = (ctx->block_cost || ctx->force_block) ? 1 : 0;
   P.qblk2 = ctx->d_qblk2.p;
   P.rblk2 = ctx->d_rblk2.p;
@@ -1321,7 +1325,8 @@ int enqueue_step(dlmpc_ctx *ctx, const Params &P, bool with_stats, bool events, 
 // pointers and options.
 int graph_step(dlmpc_ctx *ctx, const Params &P, bool with_stats) {
   dlmpc_ctx::GraphKey key{P.x, P.u, P.x_next, P.warm, with_stats, ctx->plan_version, P.fixed_iters, P.max_iter,
-                          P.Phi != nullptr, P.trace != nullptr, P.compact, P.block_cost};
+                          P.Phi != nullptr, P.trace != nullptr, P.compact, P.block_cost, P.stale_thr,
+                          P.stale_seed};
   for (auto &ge : ctx->graphs)
     if (ge.key == key) {
       CK(cudaGraphLaunch(ge.exec, ctx->stream), "cudaGraphLaunch");
@@ -1588,6 +1593,15 @@ extern "C" int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value) {
     case DLMPC_OPT_TEST_SKIP_ARRIVAL: ctx->skip_arrival_cta = (int)value; return 0;
     case DLMPC_OPT_COMPACT: ctx->compact = value != 0; return 0;
     case DLMPC_OPT_BLOCK_PHI: ctx->force_block = value != 0; return 0;
+    case DLMPC_OPT_STALE_PROB:
+      if (!(value >= 0 && value <= 1)) return ctx->fail(DLMPC_ERR_ARG, "the message-loss probability must lie in [0, 1]");
+      ctx->stale_thr = (unsigned long long)(value * 9007199254740992.0);  // floor(p 2^53)
+      return 0;
+    case DLMPC_OPT_STALE_SEED:
+      if (!(value >= 0 && value < 18446744073709551616.0) || value != std::floor(value))
+        return ctx->fail(DLMPC_ERR_ARG, "the message-loss seed must be a non-negative integer");
+      ctx->stale_seed = (unsigned long long)value;
+      return 0;
     case DLMPC_OPT_RESIDENCY: {
       if (!(value >= 0 && value <= 2)) return ctx->fail(DLMPC_ERR_ARG, "residency must be 0, 1 or 2");
       const int old = ctx->residency;
@@ -1701,6 +1715,7 @@ extern "C" int dlmpc_run_variant(dlmpc_ctx *ctx, int32_t variant, const float *x
   for (const Item &it : ctx->items)
     if (it.k > 256) return ctx->fail(DLMPC_ERR_ARG, "variants need null spaces of dimension <= 256");
   if (ctx->block_cost) return ctx->fail(DLMPC_ERR_ARG, "the paper variants take diagonal cost weights only");
+  if (ctx->stale_thr) return ctx->fail(DLMPC_ERR_ARG, "the paper variants exchange every message");
   if (!ctx->d_phi.p || ctx->d_phi.n != (size_t)ctx->state_floats) {
     CK(ctx->d_phi.alloc(ctx->state_floats), "alloc Phi");
     CK(cudaMemsetAsync(ctx->d_phi.p, 0, ctx->state_floats * 4, s), "memset");

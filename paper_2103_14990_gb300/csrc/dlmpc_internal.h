@@ -108,6 +108,11 @@ struct Params {
   int32_t skip_arrival_cta;   // test of the bounded waits: this CTA leaves before its first
                               // iteration barrier (-1 = none)
   int32_t compact;            // != 0: iterations after the first use the compact iterate
+  // simulated lost messages: the row sums patch j sends to member m at the end
+  // of iteration k are lost when SplitMix64 draw (k N + j) N + m of stale_seed,
+  // shifted right by 11, is below stale_thr (0: none); the receiver keeps the
+  // value it holds
+  unsigned long long stale_thr, stale_seed;
   int32_t block_cost;         // != 0: Phi-step by slot box-QP with the full cost blocks
   const float *qblk2, *rblk2; // [sub][nx][nx] 2 Q_i, [sub][nu][nu] 2 R_i
   // explicit solution of the slot QP with coupled rows (null: boxes only);

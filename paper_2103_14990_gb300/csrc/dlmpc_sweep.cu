@@ -197,6 +197,27 @@ __device__ __forceinline__ const float *cached_extra(const float *icache, int wi
   return icache + wi * kItemFloats + (int)((sizeof(Item) + 3) / 4);
 }
 
+// Simulated lost messages (the fully distributed setting, Sec. V): output n
+// of SplitMix64 (Steele, Lea and Flood, 2014) seeded with `seed` ...
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
+  uint64_t z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// ... decides whether the row sums patch j sends to member m at the end of
+// iteration k are lost: draw n = (k N + j) N + m, lost when its top 53 bits
+// are below the threshold floor(p 2^53).  A lost message leaves the value the
+// receiver holds, so the writer copies the slot's current value forward.
+__device__ __forceinline__ float send(const Params &P, int iter, int j, int m, int idx, float fresh) {
+  if (P.stale_thr == 0ull) return fresh;
+  const uint64_t N = (uint64_t)P.n_items;
+  const uint64_t n = ((uint64_t)iter * N + (uint64_t)j) * N + (uint64_t)m;
+  const float *Gcur = (iter & 1) ? P.G1 : P.G0;  // read this iteration, the receiver's value
+  return (splitmix64_at(P.stale_seed, n) >> 11) < P.stale_thr ? __ldcg(Gcur + idx) : fresh;
+}
+
 // Phi-comp for every row of one patch (Sec. II-A row problem, closed form):
 // w = (Psi - Lambda)_r . x_hat from the exchange sums, z = clip(rho w / (rho +
 // 2 q s), lo, hi), alpha = (z - w) / s (0 when s = 0).  The new Phi row is
@@ -843,7 +864,8 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
       rsum = fmaf(ps, xj[c], rsum);
     }
     if (cp && r >= NX) cp[cpl + red] = rsum;
-    Gnext[reinterpret_cast<const int *>(tab + mpos * MT)[3] + r] = gsum;
+    const int gi = reinterpret_cast<const int *>(tab + mpos * MT)[3] + r;
+    Gnext[gi] = send(P, iter, it.sub, P.members[it.mem_off + mpos], gi, gsum);
   }
   finish_item<GT>(P, idx, it, extra, G, prim_f, dual_f, g, gt, lnc, iter);
 }
@@ -939,7 +961,8 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
       const float rn = fmaf(s, o, Rv[red]);
       Rv[red] = rn;
       lhat[red] = lh;
-      Gnext[reinterpret_cast<const int *>(rt + red * kRowRecord)[2]] = fmaf(-s, lh, rn);
+      const int gi = reinterpret_cast<const int *>(rt + red * kRowRecord)[2];
+      Gnext[gi] = send(P, iter, it.sub, P.members[it.mem_off + small_div(red, rs_red)], gi, fmaf(-s, lh, rn));
     }
   }
   // slot-0 rows: Psi fixed (e_c on the own member), lhat = alpha
@@ -962,7 +985,8 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
 #pragma unroll
     for (int c = 0; c < NX; ++c)
       if (aux == c) own = xj[c];
-    Gnext[reinterpret_cast<const int *>(rt + p * kRowRecord)[2]] = fmaf(-s, a, own);
+    const int gi = reinterpret_cast<const int *>(rt + p * kRowRecord)[2];
+    Gnext[gi] = send(P, iter, it.sub, P.members[it.mem_off + small_div(p - dred, NX)], gi, fmaf(-s, a, own));
   }
   finish_item<GT>(P, idx, it, extra, G, prim_f, dual_f, g, gt, lnc, iter);
 }

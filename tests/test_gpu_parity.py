@@ -597,3 +597,61 @@ def test_coupled_in_a_batch_with_a_plain_instance(torch):
         off_s += n
         off_u += p.n_sub
     s.close()
+
+
+# --------------------------------------------------------------------------
+# Simulated lost messages (the distributed setting of Sec. V): the receiver
+# keeps the last row sums it got; SplitMix64 draws on both sides
+# --------------------------------------------------------------------------
+
+STALE_CASES = {
+    "chain16_T10_d3_box": lambda: SMALL["chain16_T10_d3_box"](),
+    "grid5x5_T6_d2_box": lambda: SMALL["grid5x5_T6_d2_box"](),
+    "chain16_T10_d3_box_blk": lambda: BLOCK["chain16_T10_d3_box_blk"](),
+}
+
+
+@pytest.mark.parametrize("name", list(STALE_CASES))
+@pytest.mark.parametrize("K,prob", [(1, 0.3), (7, 0.3), (40, 0.3), (25, 1.0)])
+def test_stale_messages_fixed_iterations_parity(name, K, prob, torch):
+    import paper_2103_14990_gb300 as pkg
+    p = STALE_CASES[name]()
+    o = O.Oracle(p)
+    ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=K, stale=(prob, 1234))
+    s = gpu_solver([p], torch)
+    s.set_option(pkg.OPT_STALE_PROB, prob)
+    s.set_option(pkg.OPT_STALE_SEED, 1234)
+    rc, st, phi, psi, lam, u, xn = run_fixed(s, torch, p.x0, K)
+    assert rel(psi, ref.Psi) <= REL and rel(phi, ref.Phi) <= REL
+    assert rel(lam, ref.Lam) <= REL or np.linalg.norm(ref.Lam) < 1e-6
+    u_ref = o.control(ref)
+    assert rel(u, u_ref) <= REL or np.max(np.abs(u - u_ref)) < 1e-7
+    rc, st, _, psi2, lam2, u2, _ = run_fixed(s, torch, p.x0, K, export=False)
+    assert rel(psi2, ref.Psi) <= REL
+    assert rel(lam2, ref.Lam) <= REL or np.linalg.norm(ref.Lam) < 1e-6
+    s.close()
+
+
+def test_stale_messages_change_the_iterates_and_p0_is_exact(torch):
+    import paper_2103_14990_gb300 as pkg
+    p = SMALL["grid5x5_T6_d2_box"]()
+    s = gpu_solver([p], torch)
+    _, _, phi_a, psi_a, _, u_a, _ = run_fixed(s, torch, p.x0, 20)
+    s.set_option(pkg.OPT_STALE_SEED, 5)
+    s.set_option(pkg.OPT_STALE_PROB, 0.0)
+    _, _, phi_b, psi_b, _, u_b, _ = run_fixed(s, torch, p.x0, 20)
+    assert np.array_equal(psi_a, psi_b) and np.array_equal(phi_a, phi_b)
+    s.set_option(pkg.OPT_STALE_PROB, 0.25)
+    _, _, phi_c, psi_c, _, u_c, _ = run_fixed(s, torch, p.x0, 20)
+    assert np.max(np.abs(psi_c - psi_a)) > 1e-5
+    # graph replay with losses: the same bits as the direct launch
+    s.set_option(pkg.OPT_GRAPH, 1)
+    _, _, phi_d, psi_d, _, u_d, _ = run_fixed(s, torch, p.x0, 20)
+    _, _, phi_e, psi_e, _, u_e, _ = run_fixed(s, torch, p.x0, 20)
+    s.set_option(pkg.OPT_GRAPH, 0)
+    assert np.array_equal(psi_c, psi_d) and np.array_equal(psi_d, psi_e)
+    with pytest.raises(pkg.DlmpcError):
+        s.set_option(pkg.OPT_STALE_PROB, 1.5)
+    with pytest.raises(pkg.DlmpcError):
+        s.run_variant(0, torch.tensor(p.x0.astype(np.float32), device="cuda"), 2)
+    s.close()
