@@ -57,9 +57,10 @@ def workload(name: str, inner_qp: str = "box"):
     return p
 
 
-def bench_config(prob, world: int, inner_qp: str = "box") -> dict:
+def bench_config(prob, world: int, inner_qp: str = "box", stale_prob: float = 0.0) -> dict:
     """The workload description shared by both arms."""
-    return {"workload": prob.name, "inner_qp": INNER_QP[inner_qp], "n_sub": prob.n_sub, "T": prob.T, "d": prob.d, "boxes": "|x|<=1, |u|<=2",
+    return {"workload": prob.name, "inner_qp": INNER_QP[inner_qp], "message_loss": stale_prob,
+            "n_sub": prob.n_sub, "T": prob.T, "d": prob.d, "boxes": "|x|<=1, |u|<=2",
             "warm_start": "previous MPC step's Psi/Lambda (step 0 cold)", "max_iter": prob.max_iter,
             "eps": prob.eps_p, "l2": "flushed between steps (256 MiB write outside the events)",
             "parallelism": "replicas" if world > 1 else "single GPU"}
@@ -169,6 +170,9 @@ def run_ours(args):
     solver = pkg.Solver([prob])
     torch.cuda.synchronize()
     t_setup = time.time() - t_setup
+    if args.stale_prob > 0:  # simulated lost messages (the distributed setting)
+        solver.set_option(pkg.OPT_STALE_PROB, args.stale_prob)
+        solver.set_option(pkg.OPT_STALE_SEED, 2021)
     n, nx, nu = prob.n_sub, prob.nx, prob.nu
     x0 = torch.tensor(prob.x0.astype(np.float32), device="cuda")
     tune = []
@@ -227,7 +231,7 @@ def run_ours(args):
 
     # ablation of the paper's GPU mappings (Sec. III): ADMM iterations/s from x(0)
     ablation = {}
-    if not args.no_ablation and args.inner_qp == "box":  # the paper's mappings take diagonal weights
+    if not args.no_ablation and args.inner_qp == "box" and args.stale_prob == 0:  # the paper's mappings
         names = {0: "naive (Sec. III-A)", 1: "combined (Sec. III-C)", 2: "persistent column patch (this library)"}
         for v, it_n in ((0, args.ablation_iters), (1, args.ablation_iters), (2, 10 * args.ablation_iters)):
             solver.run_variant(v, x0, 2)  # warm-up
@@ -238,7 +242,8 @@ def run_ours(args):
             v["speedup_vs_naive"] = round(v["admm_iters_per_s"] / base, 2)
 
     learned = (learned_line(prob, args)
-               if (not args.no_learned and rank == 0 and world == 1 and args.inner_qp == "box") else None)
+               if (not args.no_learned and rank == 0 and world == 1 and args.inner_qp == "box"
+                   and args.stale_prob == 0) else None)
 
     # e2e: host (pinned) buffers through the C ABI, H2D and D2H inside the timed region
     xh = torch.empty(n, nx, dtype=torch.float32, pin_memory=True)
@@ -260,7 +265,7 @@ def run_ours(args):
     achieved = info["iter_bytes"] * tot_iters / kern_s / 1e9
     traffic = (NCU_TRAFFIC["bytes_per_launch"]
                if NCU_TRAFFIC["src_sha256"] == kernel_sha() and NCU_TRAFFIC["workload"] == args.workload
-               and args.inner_qp == "box" else None)
+               and args.inner_qp == "box" and args.stale_prob == 0 else None)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_src, "kernel": "sweep_kernel",
@@ -272,7 +277,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_dev / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded chain plant, x0 ~ U[-0.9,0.9])",
-        "config": bench_config(prob, world, args.inner_qp),
+        "config": bench_config(prob, world, args.inner_qp, args.stale_prob),
         "admm_iters_per_s": round(tot_iters / kern_s, 1),
         "iters_per_step": round(tot_iters / args.steps, 2),
         "steps_at_max_iter": int(sum(1 for s in status if s != 0)),
@@ -292,7 +297,7 @@ def run_ours(args):
         "wall_s_timed_region": round(wall, 4),
         "clocks": clk.summary(),
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.inner_qp == "box":
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.inner_qp == "box" and args.stale_prob == 0:
         out["cpu_baseline"] = cpu_baseline(args, iters)
         out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args, iters)
     if rank == 0:
@@ -458,7 +463,7 @@ def run_reference(args):
     from oracle import dlmpc_oracle as O
     prob = workload(args.workload)
     o = O.Oracle(prob)
-    table = oracle_iters_table(args.workload) if args.inner_qp == "box" else None
+    table = oracle_iters_table(args.workload) if (args.inner_qp == "box" and args.stale_prob == 0) else None
     if table is None:
         print(json.dumps({"impl": "reference", "unavailable": "no oracle iteration table for this workload"}))
         return
@@ -501,6 +506,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="chain1024")
+    ap.add_argument("--stale-prob", type=float, default=0.0,
+                    help="probability that an exchange message is lost (the receiver keeps its value)")
     ap.add_argument("--inner-qp", choices=sorted(INNER_QP), default="box",
                     help="Phi-step cost/constraint form: box (default), block, coupled")
     ap.add_argument("--no-cpu-baseline", action="store_true")
