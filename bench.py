@@ -38,8 +38,8 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_sweep.c
 # DRAM bytes (read + write) of one sweep_kernel launch of a workload from an
 # ncu capture, and the sha256 of the kernel source it was taken on; reported
 # as null for other workloads and when the source has changed since.
-NCU_TRAFFIC = {"workload": "chain1024", "src_sha256": "0351b54762367081b71060b7f14955a5cd60bffba19b5f4ec2cb93b41ea9eff6",
-               "bytes_per_launch": 86350080}  # profiles/sweep_kernel_chain1024.md
+NCU_TRAFFIC = {"workload": "chain1024", "src_sha256": "203fb4f82149d35cde5dbb9d80364b58b12936f5a2b82bd5f4da97d58d2334b4",
+               "bytes_per_launch": 158949632}  # profiles/sweep_kernel_chain1024.md
 
 
 INNER_QP = {"box": "diagonal Q, R with boxes (closed-form row Phi-step)",
