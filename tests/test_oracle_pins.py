@@ -314,10 +314,10 @@ def test_dual_update_and_closed_loop_dynamics():
 def test_planted_dropped_cost_is_caught(monkeypatch):
     p = I.make_instance(3, 4, 2, seed=21, boxes=False, x0_dist="normal")
     orig = O.phi_step
-    def bad(lay, Psi, Lam, x0, rho):
+    def bad(lay, Psi, Lam, x0, rho, w=None):
         saved = lay.qw.copy(); lay.qw[:] = 0.0
         try:
-            return orig(lay, Psi, Lam, x0, rho)
+            return orig(lay, Psi, Lam, x0, rho, w=w)
         finally:
             lay.qw[:] = saved
     monkeypatch.setattr(O, "phi_step", bad)
