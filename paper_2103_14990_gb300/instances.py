@@ -194,6 +194,44 @@ def make_instance(n: int, T: int, d: int, *, graph: str = "chain", seed: int = 0
                    mpc_steps=mpc_steps, name=name, graph=graph, grid_shape=shape)
 
 
+def make_general(n: int, T: int, d: int, nx: int, nu: int, *, graph: str = "chain", seed: int = 0,
+                 boxes: bool = True, x_bound: float = 1.0, u_bound: float = 2.0, max_iter: int = 5000,
+                 name: str = "") -> Problem:
+    """A plant of any state and input size (1..4 each): A_ii = 0.8 I + E with
+    E ~ U[-0.1, 0.1], B_ii ~ U[0, 0.3], and couplings that enter through the
+    neighbour's input directions, A_ij = B_ii C_ij with C_ij ~ U[-0.3, 0.3]
+    (as in the chain plant, where the coupling enters the input-driven state;
+    this keeps the d-local problem feasible).  Q = I, R = I; x0 ~ U[-0.9,
+    0.9].  Draw order (numpy PCG64 `default_rng(seed)`): per subsystem E then
+    B_ii, then per CSR entry C_ij, then x0."""
+    rng = np.random.default_rng(seed)
+    if graph == "chain":
+        ptr, idx = chain_graph(n)
+        shape = None
+    else:
+        ptr, idx, shape = grid_graph(n)
+    A_diag = np.zeros((n, nx, nx))
+    B = np.zeros((n, nx, nu))
+    for i in range(n):
+        A_diag[i] = 0.8 * np.eye(nx) + rng.uniform(-0.1, 0.1, (nx, nx))
+        B[i] = rng.uniform(0.0, 0.3, (nx, nu))
+    nnz = int(ptr[-1])
+    A_off = np.zeros((nnz, nx, nx))
+    for i in range(n):
+        for e in range(ptr[i], ptr[i + 1]):
+            A_off[e] = B[i] @ rng.uniform(-0.3, 0.3, (nu, nx))
+    x0 = rng.uniform(-0.9, 0.9, (n, nx))
+    if boxes:
+        x_lo, x_hi = np.full((n, nx), -x_bound), np.full((n, nx), x_bound)
+        u_lo, u_hi = np.full((n, nu), -u_bound), np.full((n, nu), u_bound)
+    else:
+        x_lo = x_hi = u_lo = u_hi = None
+    return Problem(n_sub=n, nx=nx, nu=nu, T=T, d=d, adj_ptr=ptr, adj_idx=idx,
+                   A_diag=A_diag, A_off=A_off, B=B, q=np.ones((n, nx)), r=np.ones((n, nu)),
+                   x_lo=x_lo, x_hi=x_hi, u_lo=u_lo, u_hi=u_hi, rho=1.0, eps_p=1e-4, eps_d=1e-4,
+                   max_iter=max_iter, x0=x0, mpc_steps=10, name=name, graph=graph, grid_shape=shape)
+
+
 def with_block_costs(p: Problem, seed: int, coupling: float = 0.5) -> Problem:
     """A copy of p whose cost blocks Q_i, R_i are full symmetric positive
     definite matrices: M M^T / n + 0.5 I with M ~ U[-coupling, coupling] plus

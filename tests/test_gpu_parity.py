@@ -655,3 +655,77 @@ def test_stale_messages_change_the_iterates_and_p0_is_exact(torch):
     with pytest.raises(pkg.DlmpcError):
         s.run_variant(0, torch.tensor(p.x0.astype(np.float32), device="cuda"), 2)
     s.close()
+
+
+# --------------------------------------------------------------------------
+# Other state and input sizes: the kernels' NX = 1..4 instantiations and the
+# slot solvers of sizes 1..4
+# --------------------------------------------------------------------------
+
+GENERAL = {
+    "nx1_nu1_chain": lambda: I.make_general(8, 5, 1, 1, 1, seed=3),
+    "nx3_nu2_chain": lambda: I.make_general(8, 5, 2, 3, 2, seed=3),
+    "nx4_nu1_grid": lambda: I.make_general(9, 4, 1, 4, 1, graph="grid", seed=3),
+    "nx4_nu4_chain": lambda: I.make_general(6, 4, 1, 4, 4, seed=3),
+    "nx3_nu1_grid": lambda: I.make_general(12, 5, 2, 3, 1, graph="grid", seed=3),
+}
+
+
+@pytest.mark.parametrize("name", list(GENERAL))
+@pytest.mark.parametrize("K", [1, 7, 40])
+def test_general_shapes_fixed_iterations_parity(name, K, torch):
+    p = GENERAL[name]()
+    o = O.Oracle(p)
+    ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=K)
+    s = gpu_solver([p], torch)
+    rc, st, phi, psi, lam, u, xn = run_fixed(s, torch, p.x0, K)
+    assert rel(psi, ref.Psi) <= REL and rel(phi, ref.Phi) <= REL
+    assert rel(lam, ref.Lam) <= REL or np.linalg.norm(ref.Lam) < 1e-6
+    u_ref = o.control(ref)
+    assert rel(u, u_ref) <= REL or np.max(np.abs(u - u_ref)) < 1e-7
+    rc, st, _, psi2, lam2, u2, _ = run_fixed(s, torch, p.x0, K, export=False)
+    assert rel(psi2, ref.Psi) <= REL
+    assert rel(u2, u_ref) <= REL or np.max(np.abs(u2 - u_ref)) < 1e-7
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["nx3_nu2_chain", "nx4_nu4_chain", "nx1_nu1_chain"])
+def test_general_shapes_block_and_coupled_parity(name, torch):
+    """Full cost blocks (slot box-QP of sizes nx and nu) and coupled rows
+    (explicit solution of sizes nx and nu) on other state and input sizes."""
+    base = GENERAL[name]()
+    for p in (I.with_block_costs(base, seed=41),
+              I.with_coupled_constraints(base, seed=42, n_cx=2, n_cu=1, g_range=(0.2, 0.6))):
+        o = O.Oracle(p)
+        ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=30)
+        s = gpu_solver([p], torch)
+        rc, st, phi, psi, lam, u, xn = run_fixed(s, torch, p.x0, 30)
+        assert rel(psi, ref.Psi) <= REL and rel(phi, ref.Phi) <= REL
+        u_ref = o.control(ref)
+        assert rel(u, u_ref) <= REL or np.max(np.abs(u - u_ref)) < 1e-7
+        rc, st, _, psi2, _, u2, _ = run_fixed(s, torch, p.x0, 30, export=False)
+        assert rel(psi2, ref.Psi) <= REL
+        s.close()
+
+
+def test_general_shape_stopped_closed_loop(torch):
+    """Conv on, warm start from the previous step, u(tau) and x(tau+1) against
+    the oracle's closed loop on a plant with three states and two inputs."""
+    import paper_2103_14990_gb300 as pkg
+    p = GENERAL["nx3_nu2_chain"]()
+    o = O.Oracle(p)
+    steps = 5
+    xs, us, its, _ = o.run_mpc(steps, warm="previous")
+    s = gpu_solver([p], torch)
+    worst = 0.0
+    for tau in range(steps):
+        x = torch.tensor(xs[tau].astype(np.float32), device="cuda")
+        u = torch.zeros(p.n_sub, p.nu, device="cuda")
+        xn = torch.zeros_like(x)
+        rc, st = s.step(x, u, xn, warm=pkg.WARM_PREVIOUS if tau > 0 else pkg.WARM_COLD)
+        assert st[0]["status"] == 0
+        assert abs(st[0]["iters"] - its[tau]) <= max(3, 0.02 * its[tau])
+        worst = max(worst, rel(u.cpu().numpy(), us[tau]))
+        assert rel(xn.cpu().numpy(), o.dynamics(xs[tau], us[tau])) <= 5 * REL
+    assert worst <= 5 * REL
+    s.close()

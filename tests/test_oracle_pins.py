@@ -810,3 +810,39 @@ def test_planted_wrong_receiver_is_caught(monkeypatch):
     monkeypatch.setattr(O, "message_lost", lambda seed, thr, k, j, m, n: real(seed, thr, k, m, j, n))
     with pytest.raises(AssertionError):
         test_stale_admm_matches_per_message_loops()
+
+
+# --------------------------------------------------------------------------
+# Other state and input sizes (1..4)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nx,nu", [(1, 1), (3, 2), (4, 4), (4, 1)])
+def test_general_shapes_admm_matches_riccati(nx, nu):
+    """d >= N-1, no boxes: u(0) of the ADMM is the finite-horizon LQR gain for
+    plants of other state and input sizes."""
+    n, T = 4, 4
+    p = I.make_general(n, T, n - 1, nx, nu, seed=13, boxes=False)
+    rng = np.random.default_rng(6)
+    p.q = rng.uniform(0.5, 2.0, p.q.shape)
+    p.r = rng.uniform(0.5, 2.0, p.r.shape)
+    A, B = p.dense_A(), p.dense_B()
+    u_ref = _riccati_u0(A, B, np.diag(p.q.reshape(-1)), np.diag(p.r.reshape(-1)), T, p.x0.reshape(-1))
+    o = O.Oracle(p)
+    res = O.admm(o.lay, o.blocks, p.x0, max_iter=50000, eps_p=1e-11, eps_d=1e-11)
+    assert res.status == O.STATUS_CONVERGED
+    assert np.allclose(o.control(res).reshape(-1), u_ref, atol=1e-8)
+
+
+@pytest.mark.parametrize("nx,nu,graph,seed", [(3, 2, "chain", 8), (1, 1, "grid", 9), (4, 2, "grid", 8)])
+def test_general_shapes_invariants(nx, nu, graph, seed):
+    p = I.make_general(9, 4, 1, nx, nu, graph=graph, seed=seed)
+    o = O.Oracle(p)
+    res = O.admm(o.lay, o.blocks, p.x0, max_iter=20000, eps_p=1e-9, eps_d=1e-9)
+    assert res.status == O.STATUS_CONVERGED
+    Z = O.global_Z_AB(p)
+    Psi = o.lay.to_dense(res.Psi)
+    rhs = np.zeros((Z.shape[0], p.n_sub * p.nx)); rhs[:p.n_sub * p.nx] = np.eye(p.n_sub * p.nx)
+    assert np.max(np.abs(Z @ Psi - rhs)) < 1e-10
+    assert np.max(np.abs(res.Phi - res.Psi)) < 1e-8
+    y = o.lay.trajectory(res.Phi, p.x0)
+    assert np.all(y <= o.lay.hi + 1e-8) and np.all(y >= o.lay.lo - 1e-8)
