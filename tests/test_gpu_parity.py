@@ -729,3 +729,54 @@ def test_general_shape_stopped_closed_loop(torch):
         assert rel(xn.cpu().numpy(), o.dynamics(xs[tau], us[tau])) <= 5 * REL
     assert worst <= 5 * REL
     s.close()
+
+
+def test_solve_batch_equals_step_on_concatenated_buffers(torch):
+    """dlmpc_solve_batch (one device buffer per instance) gives the bits of
+    dlmpc_step on the concatenated buffers, state and statistics included."""
+    import paper_2103_14990_gb300 as pkg
+    probs = [SMALL["chain16_T10_d3_box"](), SMALL["grid5x5_T6_d2_box"](), I.chain10()]
+    outs = []
+    for mode in ("step", "batch"):
+        s = gpu_solver(probs, torch)
+        s.set_option(pkg.OPT_FIXED_ITERS, 17)
+        xs = [torch.tensor(p.x0.astype(np.float32), device="cuda") for p in probs]
+        us = [torch.zeros(p.n_sub, p.nu, device="cuda") for p in probs]
+        xns = [torch.zeros(p.n_sub, p.nx, device="cuda") for p in probs]
+        if mode == "step":
+            x = torch.cat(xs)
+            u = torch.zeros(x.shape[0], probs[0].nu, device="cuda")
+            xn = torch.zeros_like(x)
+            rc, st = s.step(x, u, xn, warm=pkg.WARM_COLD)
+            u_list, xn_list = list(torch.split(u, [p.n_sub for p in probs])), \
+                list(torch.split(xn, [p.n_sub for p in probs]))
+        else:
+            rc, st = s.solve_batch(xs, us, xns, warm=pkg.WARM_COLD)
+            u_list, xn_list = us, xns
+        _, psi, lam = s.get_state()
+        torch.cuda.synchronize()
+        outs.append((psi.cpu().numpy(), lam.cpu().numpy(), [a.cpu().numpy() for a in u_list],
+                     [a.cpu().numpy() for a in xn_list], [(d["iters"], d["status"]) for d in st]))
+        s.close()
+    a, b = outs
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert all(np.array_equal(x, y) for x, y in zip(a[2], b[2]))
+    assert all(np.array_equal(x, y) for x, y in zip(a[3], b[3]))
+    assert a[4] == b[4]
+
+
+def test_set_state_continues_from_the_given_iterate(torch):
+    """Psi and Lambda written with dlmpc_set_state are the start of the next
+    warm step: K more iterations equal the oracle's K iterations from that
+    state."""
+    import paper_2103_14990_gb300 as pkg
+    p = SMALL["grid5x5_T6_d2_box"]()
+    o = O.Oracle(p)
+    mid = O.admm(o.lay, o.blocks, p.x0, fixed_iters=9)
+    ref = O.admm(o.lay, o.blocks, p.x0, Psi0=mid.Psi, Lam0=mid.Lam, fixed_iters=11)
+    s = gpu_solver([p], torch)
+    s.set_state(torch.tensor(mid.Psi.astype(np.float32), device="cuda"),
+                torch.tensor(mid.Lam.astype(np.float32), device="cuda"))
+    rc, st, phi, psi, lam, u, xn = run_fixed(s, torch, p.x0, 11, warm=pkg.WARM_PREVIOUS)
+    assert rel(psi, ref.Psi) <= REL and rel(phi, ref.Phi) <= REL and rel(lam, ref.Lam) <= REL
+    s.close()
