@@ -275,8 +275,8 @@ def run_ours(args):
                 "peak_source": peak_src, "kernel": "sweep_kernel",
                 "algorithmic_bytes_per_iter": info["iter_bytes"],
                 "mean_launch_ms": round(sum(kms) / len(kms), 4),
-                "note": "operators resident in shared memory and L2: DRAM sees traffic/(frac x peak x time) "
-                        "of the algorithmic bytes; the loop is on-chip latency-bound (onchip)",
+                "note": "the operators stay in shared memory and L2: DRAM moves `traffic` bytes per launch, "
+                        "far below the algorithmic bytes; the loop is bound by on-chip latency (onchip)",
                 "onchip": NCU_TRAFFIC["onchip"] if ncu_current else None}
 
     out = {
