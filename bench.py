@@ -549,7 +549,10 @@ def main():
     ap.add_argument("--learn-steps", type=int, default=36)
     ap.add_argument("--learn-epochs", type=int, default=40)
     ap.add_argument("--ablation-iters", type=int, default=20)
-    ap.add_argument("--tune-iters", type=int, default=20)
+    # the autotuner's fixed iteration count: near the steps' own (about 350 on
+    # the chain) so that a plan's one-time prologue (bulk copies of resident
+    # N) weighs as it does in the timed loop
+    ap.add_argument("--tune-iters", type=int, default=200)
     ap.add_argument("--sample-seconds", type=float, default=15.0)
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--reference-worker", action="store_true", help=argparse.SUPPRESS)

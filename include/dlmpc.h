@@ -338,6 +338,9 @@ typedef struct {
  * residency, runs `iters` fixed ADMM iterations from a cold start on x_dev
  * (device, [n_sub_total][nx]), times the kernel with CUDA events, keeps the
  * fastest plan and caches it per problem signature for the process.
+ * A plan's one-time prologue (bulk copies of resident N) is part of each
+ * timing, so `iters` near the steps' own iteration count ranks the plans as
+ * the steps will see them.
  * iters <= 0 applies the cached choice without measuring.  Psi and Lambda are
  * restored afterwards.  entries (host, may be NULL) receives up to `cap`
  * measured shapes.  Returns the number measured, or an error.  Synchronous. */

@@ -307,7 +307,9 @@ class Solver:
 
     def autotune(self, x, iters: int = 20):
         """Times every feasible sweep launch shape on `x` (CUDA tensor) and keeps
-        the fastest; returns the measured table (fastest first)."""
+        the fastest; returns the measured table (fastest first).  `iters` near
+        the steps' own iteration count weighs each plan's one-time prologue as
+        the steps will."""
         cap = 512
         arr = (TuneEntry_C * cap)()
         n = self._check(self.lib.dlmpc_autotune(self._ctx, ctypes.c_void_p(x.data_ptr()), iters, arr, cap))
