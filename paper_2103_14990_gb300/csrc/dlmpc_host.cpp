@@ -849,20 +849,16 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
     insts.erase(std::unique(insts.begin(), insts.end()), insts.end());
     max_li = std::max<int>(max_li, (int)insts.size());
   }
-  int64_t max_n = 4;
-  for (const Item &it : ctx->items) max_n = std::max<int64_t>(max_n, (int64_t)it.dred_pad * it.kpad);
   const int cta_floats = 8 + 4 * ((3 * max_li + 3) / 4);
-  (void)max_n;  // N that is not resident is read from global memory directly
   int64_t used_max = 0;
   std::vector<std::vector<std::vector<int32_t>>> groups(grid);
-  for (int pass = 0; pass < 2; ++pass) {
+  {  // N that is not resident is read from global memory directly
     const int grp = sweep_group_floats(nx, ctx->nu, gt, wave, ctx->max_dcol, ctx->max_dred_pad, ctx->max_kpad,
                                        ctx->max_nmem);
     const int64_t arena_cap = budget - (int64_t)ng * grp - cta_floats;
     if (arena_cap < 0) return ctx->fail(DLMPC_ERR_ARG, "shared-memory budget exceeded by the group buffers");
     used_max = 0;
     ctx->resident_n_items = ctx->resident_state_items = 0;
-    bool any_streamed = false;
     for (int b = 0; b < grid; ++b) {
       groups[b] = lpt(ctx, ctas[b], ng);
       int64_t used = 0;
@@ -893,8 +889,6 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
           it.n_sm = (int32_t)used;
           used += need;
           ++ctx->resident_n_items;
-        } else {
-          any_streamed = true;
         }
       }
       for (int id : rr) {
@@ -912,9 +906,7 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
       for (auto &gl : groups[b])
         std::stable_partition(gl.begin(), gl.end(), [&](int id) { return ctx->items[id].n_sm >= 0; });
     }
-    (void)any_streamed;
     ctx->grp_floats = grp;
-    break;
   }
   ctx->grid = grid;
   ctx->gt = gt;

@@ -218,10 +218,6 @@ __device__ __forceinline__ float send(const Params &P, int iter, int j, int m, i
   return (splitmix64_at(P.stale_seed, n) >> 11) < P.stale_thr ? __ldcg(Gcur + idx) : fresh;
 }
 
-// Phi-comp for every row of one patch (Sec. II-A row problem, closed form):
-// w = (Psi - Lambda)_r . x_hat from the exchange sums, z = clip(rho w / (rho +
-// 2 q s), lo, hi), alpha = (z - w) / s (0 when s = 0).  The new Phi row is
-// Psi_r - Lambda_r + alpha x_hat; only alpha is stored.
 // Closed form of one row from its w and row record (see phi_rows).
 __device__ __forceinline__ void phi_row(const Params &P, int p, int dred, int aux, float4 c, float w,
                                         float *alpha_out) {
