@@ -248,6 +248,8 @@ def run_ours(args):
     learned = (learned_line(prob, args)
                if (not args.no_learned and rank == 0 and world == 1 and args.inner_qp == "box"
                    and args.stale_prob == 0) else None)
+    batched = (batched_line(prob, args, flush)
+               if (args.batch > 1 and args.stale_prob == 0 and rank == 0 and world == 1) else None)
 
     # e2e: host (pinned) buffers through the C ABI, H2D and D2H inside the timed region
     xh = torch.empty(n, nx, dtype=torch.float32, pin_memory=True)
@@ -294,6 +296,7 @@ def run_ours(args):
         "graph": graph,
         "ablation": ablation,
         "learned": learned,
+        "batched": batched,
         "sweep": {"group_threads": info["group_threads"], "groups_per_cta": info["groups_per_cta"],
                   "wave": info["wave"], "grid_ctas": info["grid_ctas"], "smem_bytes": info["smem_bytes"],
                   "resident_n_items": info["resident_n_items"],
@@ -311,6 +314,45 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def batched_line(prob, args, flush):
+    """Several instances of the workload (the same plant, different x(0)) in
+    one context: one launch per MPC step advances every instance's closed
+    loop, an instance at rest once its ADMM has converged.  Instance-steps per
+    second against the single-instance line."""
+    import numpy as np
+    import torch
+    import dataclasses
+    import paper_2103_14990_gb300 as pkg
+    from paper_2103_14990_gb300 import instances as I
+    B = args.batch
+    x0s = I.random_x0(prob.n_sub, B, seed=3000)
+    probs = [dataclasses.replace(prob, x0=x0s[b]) for b in range(B)]
+    s = pkg.Solver(probs)
+    x = torch.tensor(np.concatenate([p.x0 for p in probs]).astype(np.float32), device="cuda")
+    s.autotune(x, iters=args.tune_iters)
+    s.set_option(pkg.OPT_TIMING, 1)
+    xn = torch.empty_like(x)
+    u = torch.empty(x.shape[0], prob.nu, device="cuda")
+    steps = max(3, args.steps // 5)
+    ms, iters = 0.0, []
+    for tau in range(args.warmup + steps):
+        flush.zero_()
+        rc, st = s.step(x, u, xn, warm=(pkg.WARM_COLD if tau == 0 else pkg.WARM_PREVIOUS), stats=True)
+        if tau >= args.warmup:
+            ms += s.timing()[1]
+            iters.append([d["iters"] for d in st])
+        x, xn = xn, x
+    info = s.info()
+    s.close()
+    it = np.array(iters)
+    return {"instances": B, "steps": steps, "value": round(B * steps / (ms / 1e3), 3), "unit": "instance MPC steps/s",
+            "ms_per_step": round(ms / steps, 4), "launch_iters_per_step": round(float(it.max(axis=1).mean()), 2),
+            "instance_iters_per_step": round(float(it.mean()), 2),
+            "sweep": {"group_threads": info["group_threads"], "groups_per_cta": info["groups_per_cta"],
+                      "wave": info["wave"], "resident_n_items": info["resident_n_items"]},
+            "x0": "U[-0.9, 0.9] per instance (seed 3000); closed loops from x(0), warm start from the previous step"}
 
 
 def learned_line(prob, args):
@@ -545,6 +587,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--batch", type=int, default=8, help="instances of the batched line (1: none)")
     ap.add_argument("--learn-replicas", type=int, default=8)
     ap.add_argument("--learn-steps", type=int, default=36)
     ap.add_argument("--learn-epochs", type=int, default=40)
