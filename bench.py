@@ -349,6 +349,7 @@ def batched_line(prob, args, flush):
     it = np.array(iters)
     return {"instances": B, "steps": steps, "value": round(B * steps / (ms / 1e3), 3), "unit": "instance MPC steps/s",
             "ms_per_step": round(ms / steps, 4), "launch_iters_per_step": round(float(it.max(axis=1).mean()), 2),
+            "instance_admm_iters_per_s": round(float(it.sum()) / (ms / 1e3), 1),
             "instance_iters_per_step": round(float(it.mean()), 2),
             "sweep": {"group_threads": info["group_threads"], "groups_per_cta": info["groups_per_cta"],
                       "wave": info["wave"], "resident_n_items": info["resident_n_items"]},
