@@ -280,7 +280,9 @@ __device__ __forceinline__ void phi_rows(const Params &P, const Item &it, const 
   }
 }
 
-// argmin 1/2 z^T (C + cd I) z - cd w^T z  s.t.  lo <= z <= hi  (N <= 4,
+constexpr int kMaxQP = 4;
+
+// argmin 1/2 z^T (C + cd I) z - cd w^T z  s.t.  lo <= z <= hi  (N <= kMaxQP,
 // C symmetric positive semi-definite, cd > 0): every component free, at lo or
 // at hi (finite bounds only).  A pattern's candidate solves the N x N system
 // whose free rows are those of C + cd I (right-hand side cd w) and whose fixed
@@ -555,139 +557,6 @@ __device__ __forceinline__ void slot_explicit(const Params &P, int key, bool slo
   }
 }
 
-// The explicit solution of one slot evaluated by kSlotLanes consecutive lanes
-// (a slot may have tens of regions): lane `sub` takes regions sub, sub + L,
-// ..., and after each round of L regions the lanes stop once one of them has
-// met the KKT test (feasible, multipliers >= 0).  The slot's z is that of the
-// lowest region index meeting it, else that of the feasible region of least
-// objective, as in slot_explicit.  `mask`: the slot's L lanes.
-constexpr int kSlotLanes = 4;
-
-template <int N>
-__device__ __forceinline__ void slot_explicit_lanes(const Params &P, int key, bool slot0, const float *C, float cd,
-                                                    const float (&w)[N], float (&z_out)[N], int sub,
-                                                    unsigned mask) {
-  const int nreg = slot0 ? 1 : P.rg_cnt[key];
-  const int nrow = slot0 ? 0 : P.rw_cnt[key];
-  const int cs = P.crow_stride;
-  const int base = P.rg_base[key];
-  const float *rows = P.crow + (int64_t)P.rw_base[key] * cs;
-  int kkt_r = 0x7fffffff;
-  float best = INFINITY, zb[N];
-#pragma unroll
-  for (int a = 0; a < N; ++a) zb[a] = w[a];
-  for (int r0 = 0; r0 < nreg; r0 += kSlotLanes) {
-    const int r = r0 + sub;
-    bool hit = false;
-    if (r < nreg) {
-      const float *tb = P.expl + (int64_t)(base + r) * P.expl_stride;
-      float z[N];
-#pragma unroll
-      for (int a = 0; a < N; ++a) {
-        float v = __ldcg(tb + N * N + a);
-#pragma unroll
-        for (int c = 0; c < N; ++c) v = fmaf(__ldcg(tb + a * N + c), w[c], v);
-        z[a] = v;
-      }
-      bool ok = true;
-      for (int j = 0; j < nrow; ++j) {
-        const float *aj = rows + j * cs;
-        float v = 0.f;
-#pragma unroll
-        for (int c = 0; c < N; ++c) v = fmaf(aj[c], z[c], v);
-        const float bj = aj[cs - 1];
-        if (v > bj + 1e-5f * fmaxf(1.f, fabsf(bj))) ok = false;
-      }
-      if (ok) {
-        const int k = r == 0 ? 0 : (int)(P.rg_desc[base + r] & 15u);
-        bool dual = true;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          if (j < k) {
-            const float lj = __ldcg(tb + 2 * N * N + N + j);
-            float mu = lj, mag = fabsf(lj);
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-              const float e = __ldcg(tb + N * N + N + j * N + c) * w[c];
-              mu += e;
-              mag += fabsf(e);
-            }
-            if (mu < -1e-5f * mag) dual = false;
-          }
-        }
-        if (dual) {
-          hit = true;
-          kkt_r = r;
-#pragma unroll
-          for (int a = 0; a < N; ++a) zb[a] = z[a];
-        } else {
-          float obj = 0.f;
-#pragma unroll
-          for (int a = 0; a < N; ++a) {
-            float hz = cd * z[a];
-#pragma unroll
-            for (int c = 0; c < N; ++c) hz = fmaf(C[a * N + c], z[c], hz);
-            obj = fmaf(z[a], 0.5f * hz - cd * w[a], obj);
-          }
-          if (obj < best) {
-            best = obj;
-#pragma unroll
-            for (int a = 0; a < N; ++a) zb[a] = z[a];
-          }
-        }
-      }
-    }
-    if (__any_sync(mask, hit)) break;
-  }
-  // the winning lane: lowest KKT region, else least objective (lowest lane on ties)
-  int kr = kkt_r;
-#pragma unroll
-  for (int o = 1; o < kSlotLanes; o <<= 1) kr = min(kr, __shfl_xor_sync(mask, kr, o));
-  bool mine;
-  if (kr != 0x7fffffff) {
-    mine = kkt_r == kr;
-  } else {
-    float b = best;
-#pragma unroll
-    for (int o = 1; o < kSlotLanes; o <<= 1) b = fminf(b, __shfl_xor_sync(mask, b, o));
-    mine = best < INFINITY && best == b;
-  }
-  const unsigned win = __ballot_sync(mask, mine);
-  if (win != 0u) {
-    const int src = __ffs(win) - 1;
-#pragma unroll
-    for (int a = 0; a < N; ++a) z_out[a] = __shfl_sync(mask, zb[a], src);
-  }
-}
-
-// One slot of the block Phi-step with coupled rows, by kSlotLanes lanes
-// (slot_solve's reads and writes; the slot's first lane writes).
-template <int N>
-__device__ __forceinline__ void slot_solve_lanes(const Params &P, int key, bool slot0, int p0, int dred,
-                                                 const float *rec, const float *C, const float *rt, float *alpha,
-                                                 float rho, int sub, unsigned mask) {
-  float w[N], z[N];
-  int aux[N];
-#pragma unroll
-  for (int a = 0; a < N; ++a) {
-    const int p = p0 + a;
-    w[a] = alpha[p];
-    aux[a] = reinterpret_cast<const int *>(rt + p * kRowRecord)[3];
-    z[a] = w[a];
-  }
-  const float inv_s = rec[2];
-  if (inv_s > 0.f) slot_explicit_lanes<N>(P, key, slot0, C, rho * inv_s, w, z, sub, mask);
-  __syncwarp(mask);  // every lane of the slot has read w
-  if (sub == 0) {
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-      const int p = p0 + a;
-      alpha[p] = inv_s > 0.f ? (z[a] - w[a]) * inv_s : 0.f;
-      if (aux[a] >= 0 && p < dred) P.u[aux[a]] = z[a];
-    }
-  }
-}
-
 // One slot of the block Phi-step: its N rows start at reduced position p0 and
 // hold w (from the row pass) in alpha; the slot QP gives z, and alpha becomes
 // (z - w)/s per row (0 when s = 0); own slot-0 inputs also give u(tau).
@@ -735,38 +604,6 @@ __device__ void phi_slots(const Params &P, const Item &it, const float *tab, con
   // the state slots of every member first, then the input slots: the costly
   // state slots share the first round over the group's threads
   const int nst = it.n_mem * T;
-  if (P.expl) {  // coupled rows: kSlotLanes lanes per slot
-    const int sub = gt & (kSlotLanes - 1);
-    const unsigned mask = ((1u << kSlotLanes) - 1u) << ((threadIdx.x & 31) & ~(kSlotLanes - 1));
-    for (int e = gt; e < it.n_mem * (2 * T - 1) * kSlotLanes; e += GT) {
-      const int g = e / kSlotLanes;
-      int mpos, kk;
-      if (g < nst) {
-        mpos = small_div(g, T);
-        kk = g - mpos * T;
-      } else {
-        mpos = small_div(g - nst, T - 1);
-        kk = T + (g - nst - mpos * (T - 1));
-      }
-      const float *rec = tab + mpos * MT;
-      const float *C = rec + 4 + 4 * NX + 3 * nu;
-      const int key = 2 * P.members[it.mem_off + mpos];
-      if (kk < T) {
-        const int p0 = kk == 0 ? dred + mpos * NX : mpos * rs_red + (kk - 1) * NX;
-        slot_solve_lanes<NX>(P, key, kk == 0, p0, dred, rec, C, rt, alpha, rho, sub, mask);
-      } else {
-        const int p0 = mpos * rs_red + (T - 1) * NX + (kk - T) * nu;
-        C += NX * NX;
-        switch (nu) {
-          case 1: slot_solve_lanes<1>(P, key + 1, false, p0, dred, rec, C, rt, alpha, rho, sub, mask); break;
-          case 2: slot_solve_lanes<2>(P, key + 1, false, p0, dred, rec, C, rt, alpha, rho, sub, mask); break;
-          case 3: slot_solve_lanes<3>(P, key + 1, false, p0, dred, rec, C, rt, alpha, rho, sub, mask); break;
-          default: slot_solve_lanes<4>(P, key + 1, false, p0, dred, rec, C, rt, alpha, rho, sub, mask); break;
-        }
-      }
-    }
-    return;
-  }
   for (int g = gt; g < it.n_mem * (2 * T - 1); g += GT) {
     int mpos, kk;
     if (g < nst) {
