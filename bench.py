@@ -442,6 +442,25 @@ def oracle_sample(workload_name: str, seconds: float, min_iters: int):
     return t_iter, done, time.perf_counter() - t1
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def _single_thread_env():
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
@@ -466,7 +485,7 @@ def cpu_baseline(args, gpu_iters):
         its = gpu_iters
         src = "the GPU run's per-step iteration counts"
     t = sum(i * s["t_iter"] + s["t_tail"] for i in its)
-    return {"value": round(len(its) / t, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": round(len(its) / t, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"{s['iters']} FP64 oracle ADMM iterations from x(0) ({s['t_iter'] * 1e3:.1f} ms each, "
                       f"one thread), scaled by {src} over the {len(its)} timed steps; one-time precompute excluded",
             "oracle_admm_iters_per_s": round(1.0 / s["t_iter"], 3)}
@@ -493,7 +512,7 @@ def cpu_baseline_all_cores(args, gpu_iters, cores=None):
     its = table["previous"]["iters"][:args.steps] if table is not None else gpu_iters
     agg = sum(rates)                       # oracle ADMM iterations per second over all cores
     t = sum(i / agg + max(tails) / cores for i in its)
-    return {"value": round(len(its) / t, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": round(len(its) / t, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"{cores} single-threaded oracle processes at once, each timing FP64 ADMM iterations from "
                       f"x(0) for {args.sample_seconds:g} s; aggregate {agg:.1f} iterations/s scaled by the same "
                       f"per-step iteration counts as cpu_baseline",
@@ -568,7 +587,7 @@ def run_reference(args):
         "data": "synthetic (seeded chain plant, x0 ~ U[-0.9,0.9])", "impl": "reference",
         "config": bench_config(prob, int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
