@@ -485,7 +485,8 @@ def cpu_baseline(args, gpu_iters):
         its = gpu_iters
         src = "the GPU run's per-step iteration counts"
     t = sum(i * s["t_iter"] + s["t_tail"] for i in its)
-    return {"value": round(len(its) / t, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+    return {"value": round(len(its) / t, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"{s['iters']} FP64 oracle ADMM iterations from x(0) ({s['t_iter'] * 1e3:.1f} ms each, "
                       f"one thread), scaled by {src} over the {len(its)} timed steps; one-time precompute excluded",
             "oracle_admm_iters_per_s": round(1.0 / s["t_iter"], 3)}
@@ -512,7 +513,8 @@ def cpu_baseline_all_cores(args, gpu_iters, cores=None):
     its = table["previous"]["iters"][:args.steps] if table is not None else gpu_iters
     agg = sum(rates)                       # oracle ADMM iterations per second over all cores
     t = sum(i / agg + max(tails) / cores for i in its)
-    return {"value": round(len(its) / t, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+    return {"value": round(len(its) / t, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"{cores} single-threaded oracle processes at once, each timing FP64 ADMM iterations from "
                       f"x(0) for {args.sample_seconds:g} s; aggregate {agg:.1f} iterations/s scaled by the same "
                       f"per-step iteration counts as cpu_baseline",
