@@ -38,7 +38,7 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_sweep.c
 # DRAM bytes (read + write) of one sweep_kernel launch of a workload from an
 # ncu capture, and the sha256 of the kernel source it was taken on; reported
 # as null for other workloads and when the source has changed since.
-NCU_TRAFFIC = {"workload": "chain1024", "src_sha256": "b8ebb4d3cf12e0be0ae7c7a7fa4a74271644a23e055f9a873e421e202c5609c5",
+NCU_TRAFFIC = {"workload": "chain1024", "src_sha256": "82fb4a1ebcf2a59f25bf54a70c1e95e4fb0e1907e249160eb066d13d18dfed25",
                "bytes_per_launch": 158949632,  # profiles/sweep_kernel_chain1024.md
                # the same kernel's on-chip load from the full capture (50 fixed
                # iterations, same launch shape): where the loop's bytes are served

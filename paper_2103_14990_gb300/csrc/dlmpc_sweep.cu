@@ -25,6 +25,12 @@
 // rotating 64-bit counters with a release reduction: the low half counts
 // arrivals, the high half sums the not-converged patches, so the global Conv
 // decision needs no extra atomic or barrier.  Every wait is bounded.
+//
+// Variants.  The block instantiation (BLK) solves the Phi-step per (member,
+// time slot) for full cost blocks, over the slot's box (slot_box_qp) or, with
+// coupled rows, by the explicit solution that the prologue rebuilds for this
+// x(tau) (build_region, slot_explicit).  Simulated lost messages (send) keep
+// the receiver's last row sums in place of a fresh exchange value.
 #include <cuda_runtime.h>
 #include <cmath>
 #include <cstdint>
