@@ -148,7 +148,8 @@ struct FactorParams {
   int32_t *rank;              // [n_items]
   int32_t *nullity;           // [n_items] k actually found (must equal planned k)
   int32_t nx;
-  int32_t item_begin;         // items item_begin .. item_begin+gridDim.x-1 in this launch
+  const int32_t *order;       // [n_items] patches by decreasing work (the queue)
+  int32_t *next;              // queue position (zero before the launch)
   int32_t use_smem;           // workspace in dynamic shared memory
 };
 

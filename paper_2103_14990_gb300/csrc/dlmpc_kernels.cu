@@ -28,10 +28,8 @@ namespace dlmpc {
 
 constexpr int kFactorThreads = 256;
 
-__global__ void __launch_bounds__(kFactorThreads) factor_kernel(FactorParams p) {
+__device__ void factor_item(const FactorParams &p, int item_id) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int item_id = p.item_begin + blockIdx.x;
-  if (item_id >= p.n_items) return;
   const Item it = p.items[item_id];
   const int D = it.dred;
   const int m = it.mrows;
@@ -219,6 +217,21 @@ __global__ void __launch_bounds__(kFactorThreads) factor_kernel(FactorParams p) 
     apply_Q(z);
     for (int i = lane; i < D; i += 32) nout[(int64_t)i * kub + e] = (float)z[i];
     __syncwarp();
+  }
+}
+// Persistent: every CTA takes the next patch from a queue ordered by
+// decreasing work (D m^2) until none is left, so large patches start first
+// and no launch waits on its slowest patch; each CTA keeps its workspace slot.
+__global__ void __launch_bounds__(kFactorThreads) factor_kernel(FactorParams p) {
+  __shared__ int next_sh;
+  for (;;) {
+    if (threadIdx.x == 0) next_sh = atomicAdd(p.next, 1);
+    __syncthreads();
+    const int k = next_sh;
+    __syncthreads();
+    if (k >= p.n_items) break;
+    factor_item(p, p.order[k]);
+    __syncthreads();
   }
 }
 
