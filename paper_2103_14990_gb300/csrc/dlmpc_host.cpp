@@ -1118,20 +1118,15 @@ extern "C" int dlmpc_precompute(dlmpc_ctx *ctx) {
   int dev = 0, sms = 1;
   CK(cudaGetDevice(&dev), "cudaGetDevice");
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
-  const int64_t budget = (int64_t)4 << 30;
+  const int64_t budget = (int64_t)8 << 30;  // factorisation workspace, freed after precompute
   // the queue: patches by decreasing work D m^2 (large ones first)
   std::vector<int32_t> order(ctx->n_sub);
   std::iota(order.begin(), order.end(), 0);
   auto work = [&](int g) { return (double)scratch[g].dred * (double)scratch[g].mrows * (double)scratch[g].mrows; };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
-  // concurrency: enough CTAs for every SM, and, above that, no more than keep
-  // the patch matrices in flight (D m doubles each, median patch) within L2
-  std::vector<double> foot(ctx->n_sub);
-  for (int g = 0; g < ctx->n_sub; ++g) foot[g] = 8.0 * scratch[g].dred * scratch[g].mrows;
-  std::nth_element(foot.begin(), foot.begin() + foot.size() / 2, foot.end());
-  const int64_t l2_fit =
-      std::max<int64_t>(sms, (int64_t)(96.0 * (1 << 20) / std::max(1.0, foot[foot.size() / 2])));
-  int conc = (int)std::min<int64_t>({(int64_t)ctx->n_sub, (int64_t)sms * 4, l2_fit,
+  // four CTAs per SM (the trailing-matrix updates are memory-bound, more
+  // patches in flight hide their latency), within the workspace budget
+  int conc = (int)std::min<int64_t>({(int64_t)ctx->n_sub, (int64_t)sms * 4,
                                      std::max<int64_t>(1, budget / (ws_stride * 8))});
   CK(d_ws.alloc((size_t)conc * ws_stride), "alloc factor workspace");
   DevBuf<int32_t> d_order, d_next;
