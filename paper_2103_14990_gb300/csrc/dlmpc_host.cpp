@@ -1152,7 +1152,8 @@ extern "C" int dlmpc_precompute(dlmpc_ctx *ctx) {
   fp.use_smem = 0;
   fp.order = d_order.p;
   fp.next = d_next.p;
-  CK(launch_factor(fp, conc, 0, s), "factor_kernel");
+  // dynamic shared memory: the current Householder vector (max_D doubles)
+  CK(launch_factor(fp, conc, (size_t)max_D * 8, s), "factor_kernel");
   std::vector<double> feas(ctx->n_sub);
   std::vector<int32_t> nul(ctx->n_sub);
   CK(cudaMemcpyAsync(feas.data(), d_feas.p, 8 * feas.size(), cudaMemcpyDeviceToHost, s), "D2H");

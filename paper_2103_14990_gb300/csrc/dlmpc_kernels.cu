@@ -134,7 +134,10 @@ __device__ void factor_item(const FactorParams &p, int item_id) {
     }
     __syncthreads();
     const double bk = beta[kk], vh = vhead[kk];
-    const double *vcol = M + (int64_t)kk * D;  // v_i = vcol[i] for i > kk
+    // v_i (i > kk) staged in shared memory: every warp reads it once per column
+    double *vcol = reinterpret_cast<double *>(smem_raw) + (p.use_smem ? (int64_t)D * m : 0);
+    for (int i = kk + 1 + tid; i < D; i += blockDim.x) vcol[i] = M[(int64_t)kk * D + i];
+    __syncthreads();
     for (int c = kk + 1 + warp; c < m; c += nwarps) {
       double *col = M + (int64_t)c * D;
       double s = (lane == 0) ? vh * col[kk] : 0.0;
