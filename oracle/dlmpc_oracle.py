@@ -22,6 +22,12 @@ Pinned parts (see tests/test_oracle_pins.py):
   * admm(stale=) - p = 0 is the exchange-free admm; a per-message loop on
                     small cases gives the same iterates; the loss draws are
                     uniform and independent, at rate p; Z_AB Psi = I holds;
+  * conv_residuals / conv_met - closed-form residuals of the first
+                    iteration from a cold start (rho != 1, decoupled subsystems
+                    of different norms), a restatement with explicit loops
+                    over dense matrices, the stop at the first iteration that
+                    meets both tests; planted mistakes (rho dropped, one
+                    global norm, per-column norms) fail these pins;
   * admm / mpc    - converged trajectory against the centralised
                     locality-constrained QP (least squares / SLSQP) and, for
                     d >= N-1 with no boxes, against the textbook finite-horizon
@@ -451,6 +457,23 @@ def per_subsystem_norm(lay: Layout, vals: np.ndarray) -> np.ndarray:
     return np.sqrt(sq)
 
 
+def conv_residuals(lay: Layout, Phi: np.ndarray, Psi_new: np.ndarray, Psi_old: np.ndarray,
+                   rho: float):
+    """Conv of Alg. 2 (the paper leaves the criterion open; reading: absolute
+    residuals per subsystem, no relative scaling).  For every subsystem j,
+    over the columns j owns (its nx columns, on their whole patch support):
+        r_j = ||Phi - Psi^{k+1}||_F          (primal: consensus Phi = Psi)
+        s_j = rho ||Psi^{k+1} - Psi^k||_F    (dual: change of the Psi iterate)
+    Returns the two per-subsystem arrays."""
+    return per_subsystem_norm(lay, Phi - Psi_new), rho * per_subsystem_norm(lay, Psi_new - Psi_old)
+
+
+def conv_met(r: np.ndarray, s: np.ndarray, eps_p: float, eps_d: float) -> bool:
+    """The d-local checks combined over the network: every subsystem has
+    r_j <= eps_p and s_j <= eps_d."""
+    return bool(np.max(r) <= eps_p and np.max(s) <= eps_d)
+
+
 @dataclasses.dataclass
 class AdmmResult:
     Phi: np.ndarray
@@ -571,10 +594,10 @@ def admm(lay: Layout, blocks: List[ColumnBlock], x0: np.ndarray, *,
             fresh = msg.sums(lay, Psi_new - Lam, x0)
             lost = message_lost(int(stale[1]), thr, it - 1, msg.j, msg.m, prob.n_sub)
             held = np.where(lost, held, fresh)
-        r_max = float(np.max(per_subsystem_norm(lay, Phi - Psi_new)))
-        s_max = float(rho * np.max(per_subsystem_norm(lay, Psi_new - Psi)))
+        r_j, s_j = conv_residuals(lay, Phi, Psi_new, Psi, rho)
+        r_max, s_max = float(np.max(r_j)), float(np.max(s_j))
         Psi = Psi_new
-        if fixed_iters is None and r_max <= eps_p and s_max <= eps_d:
+        if fixed_iters is None and conv_met(r_j, s_j, eps_p, eps_d):
             status = STATUS_CONVERGED
             break
     if fixed_iters is not None:

@@ -193,8 +193,12 @@ def _centralised_affine(p, x0):
     return lay, y0, np.hstack(blocks)
 
 
-def test_admm_matches_centralised_least_squares():
-    p = I.make_instance(5, 4, 1, seed=11, boxes=False, x0_dist="normal")
+@pytest.mark.parametrize("rho", [1.0, 0.7, 2.5])
+def test_admm_matches_centralised_least_squares(rho):
+    """The fixed point of ADMM does not depend on rho: every rho reaches the
+    centralised optimum (a rho used inconsistently between the Phi-step and
+    the dual update would move the fixed point)."""
+    p = I.make_instance(5, 4, 1, seed=11, boxes=False, x0_dist="normal", rho=rho)
     lay, y0, G = _centralised_affine(p, p.x0)
     W = np.sqrt(lay.qw)
     theta = np.linalg.lstsq(W[:, None] * G, -W * y0, rcond=None)[0]
@@ -206,14 +210,15 @@ def test_admm_matches_centralised_least_squares():
     assert np.allclose(y, y_ref, atol=1e-8)
 
 
-def test_admm_matches_centralised_boxed_qp():
-    """Boxed case.  The trajectory lives in y0 + range(G); with an orthonormal
+@pytest.mark.parametrize("rho", [1.0, 0.7, 2.5])
+def test_admm_matches_centralised_boxed_qp(rho):
+    """Boxed case, for several rho.  The trajectory lives in y0 + range(G); with an orthonormal
     basis Bm of range(G) the centralised QP is strictly convex in phi.  Its
     dual (lambda >= 0) is solved by L-BFGS-B; the active set it exposes is then
     solved exactly as an equality-constrained KKT system, whose multipliers
     must carry the right signs.  The instance is feasible and its unconstrained
     optimum violates the box, so the box is exercised."""
-    p = I.make_instance(4, 4, 1, seed=3, boxes=True, x0_dist="uniform", x_bound=1.0, u_bound=0.1)
+    p = I.make_instance(4, 4, 1, seed=3, boxes=True, x0_dist="uniform", x_bound=1.0, u_bound=0.1, rho=rho)
     p.x0 = 0.9 * p.x0
     lay, y0, G = _centralised_affine(p, p.x0)
     U, S, _ = np.linalg.svd(G, full_matrices=False)
@@ -846,3 +851,125 @@ def test_general_shapes_invariants(nx, nu, graph, seed):
     assert np.max(np.abs(res.Phi - res.Psi)) < 1e-8
     y = o.lay.trajectory(res.Phi, p.x0)
     assert np.all(y <= o.lay.hi + 1e-8) and np.all(y >= o.lay.lo - 1e-8)
+
+
+# --------------------------------------------------------------------------
+# Conv (Alg. 2): residuals and the stopping rule, with rho != 1
+# --------------------------------------------------------------------------
+
+def _decoupled_pair(rho):
+    """Two subsystems with no coupling edge, T = 2, d = 0, different plants,
+    no boxes: every column problem is the one-subsystem one."""
+    p = I.make_instance(2, 2, 0, seed=31, boxes=False, x0_dist="normal", rho=rho)
+    p.adj_ptr = np.zeros(3, np.int32)
+    p.adj_idx = np.zeros(0, np.int32)
+    p.A_off = np.zeros((0, 2, 2))
+    p.A_diag[1] = [[1.5, 0.8], [-0.6, 2.0]]          # a second, quite different plant
+    p.B[1] = [[0.5], [0.2]]
+    return p
+
+
+def _first_iteration_residual_by_hand(p):
+    """From a cold start the first Phi-step sees v = 0, so Phi^1 = 0 (z* = 0 is
+    inside every box), Psi^1 = q (the projection of 0 is the min-norm point of
+    Z_j psi = e_c) and r_j = ||Psi^1||_F, s_j = rho ||Psi^1 - 0||_F.  With T = 2
+    the column problem of own state c is: x_0 = e_c, x_1 = A e_c + B u_0,
+    min ||x_0||^2 + ||x_1||^2 + u_0^2, whose minimiser in u_0 is
+    u_0 = -B^T A e_c / (1 + B^T B) (one-dimensional least squares)."""
+    out = []
+    for j in range(p.n_sub):
+        A, B = p.A_diag[j], p.B[j][:, 0]
+        sq = 0.0
+        for c in range(p.nx):
+            e = np.zeros(p.nx); e[c] = 1.0
+            u = -(B @ A @ e) / (1.0 + B @ B)
+            x1 = A @ e + B * u
+            sq += 1.0 + x1 @ x1 + u * u
+        out.append(np.sqrt(sq))
+    return np.array(out)
+
+
+def test_conv_first_iteration_closed_form():
+    rho = 0.7
+    p = _decoupled_pair(rho)
+    o = O.Oracle(p)
+    r_hand = _first_iteration_residual_by_hand(p)
+    assert abs(r_hand[0] - r_hand[1]) > 0.05                 # the max picks one subsystem
+    res = O.admm(o.lay, o.blocks, p.x0, fixed_iters=1)
+    assert np.max(np.abs(res.Phi)) == 0.0
+    assert np.isclose(res.r_max, r_hand.max(), rtol=1e-12)
+    assert np.isclose(res.s_max, rho * r_hand.max(), rtol=1e-12)
+    r_j, s_j = O.conv_residuals(o.lay, res.Phi, res.Psi, np.zeros(o.lay.nnz), rho)
+    assert r_j.shape == s_j.shape == (p.n_sub,)
+    assert np.allclose(r_j, r_hand, rtol=1e-12)
+    assert np.allclose(s_j, rho * r_hand, rtol=1e-12)
+    assert np.isclose(res.r_max, r_hand.max(), rtol=1e-12)
+    assert np.isclose(res.s_max, rho * r_hand.max(), rtol=1e-12)
+    # the stopping rule: eps between the two residuals stops after one iteration
+    # exactly when both tests pass
+    lo, hi = rho * r_hand.max(), r_hand.max()
+    assert O.admm(o.lay, o.blocks, p.x0, eps_p=hi * 1.001, eps_d=lo * 1.001, max_iter=1).status == O.STATUS_CONVERGED
+    assert O.admm(o.lay, o.blocks, p.x0, eps_p=hi * 1.001, eps_d=lo * 0.999, max_iter=1).status == O.STATUS_MAX_ITER
+    assert O.admm(o.lay, o.blocks, p.x0, eps_p=hi * 0.999, eps_d=lo * 1.001, max_iter=1).status == O.STATUS_MAX_ITER
+
+
+def _residuals_by_loops(p, Phi, Psi_new, Psi_old, rho):
+    """r_j and s_j with explicit loops over the dense matrices: every entry of
+    the nx columns of subsystem j (the whole column, not only the patch)."""
+    lay = O.Layout(p)
+    F, Pn, Po = lay.to_dense(Phi), lay.to_dense(Psi_new), lay.to_dense(Psi_old)
+    r, s = np.zeros(p.n_sub), np.zeros(p.n_sub)
+    for j in range(p.n_sub):
+        for c in range(j * p.nx, (j + 1) * p.nx):
+            for row in range(F.shape[0]):
+                r[j] += (F[row, c] - Pn[row, c]) ** 2
+                s[j] += (Pn[row, c] - Po[row, c]) ** 2
+    return np.sqrt(r), rho * np.sqrt(s)
+
+
+def test_conv_stops_at_the_first_iteration_meeting_both_tests():
+    """Coupled chain with boxes and rho = 0.7, stepped one iteration at a time
+    (the iteration is a map of (Psi, Lambda)); the residuals restated with
+    loops decide the first iteration at which every subsystem meets both
+    tests, and the stopped run must end exactly there with those residuals."""
+    rho, eps = 0.7, 2e-3
+    p = I.make_instance(4, 3, 1, seed=12, boxes=True, x0_dist="uniform", rho=rho, eps=eps, u_bound=0.3)
+    o = O.Oracle(p)
+    Psi, Lam = np.zeros(o.lay.nnz), np.zeros(o.lay.nnz)
+    stop = None
+    for k in range(1, 400):
+        res = O.admm(o.lay, o.blocks, p.x0, Psi0=Psi, Lam0=Lam, fixed_iters=1)
+        r, s = _residuals_by_loops(p, res.Phi, res.Psi, Psi, rho)
+        rj, sj = O.conv_residuals(o.lay, res.Phi, res.Psi, Psi, rho)
+        assert np.allclose(rj, r, rtol=1e-10, atol=1e-15) and np.allclose(sj, s, rtol=1e-10, atol=1e-15)
+        Psi, Lam = res.Psi, res.Lam
+        if np.max(r) <= eps and np.max(s) <= eps:
+            stop = (k, np.max(r), np.max(s))
+            break
+    assert stop is not None and stop[0] > 5
+    run = O.admm(o.lay, o.blocks, p.x0)
+    assert run.status == O.STATUS_CONVERGED and run.iters == stop[0]
+    assert np.isclose(run.r_max, stop[1], rtol=1e-9) and np.isclose(run.s_max, stop[2], rtol=1e-9)
+
+
+def _plant_conv(monkeypatch, kind):
+    def bad(lay, Phi, Psi_new, Psi_old, rho):
+        if kind == "rho_dropped":
+            return O.per_subsystem_norm(lay, Phi - Psi_new), O.per_subsystem_norm(lay, Psi_new - Psi_old)
+        if kind == "global_norm":
+            n = lay.prob.n_sub
+            return (np.full(n, np.linalg.norm(Phi - Psi_new)),
+                    rho * np.full(n, np.linalg.norm(Psi_new - Psi_old)))
+        if kind == "per_column":
+            def col_norm(v):
+                return np.sqrt(np.bincount(lay.cols, weights=v * v, minlength=lay.prob.n_sub * lay.prob.nx))
+            return col_norm(Phi - Psi_new), rho * col_norm(Psi_new - Psi_old)
+        raise ValueError(kind)
+    monkeypatch.setattr(O, "conv_residuals", bad)
+
+
+@pytest.mark.parametrize("kind", ["rho_dropped", "global_norm", "per_column"])
+def test_planted_conv_mistake_is_caught(monkeypatch, kind):
+    _plant_conv(monkeypatch, kind)
+    with pytest.raises(AssertionError):
+        test_conv_first_iteration_closed_form()
