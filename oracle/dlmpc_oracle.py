@@ -189,7 +189,13 @@ def column_block(prob, j: int, rtol: float = 1e-12) -> ColumnBlock:
         for k, (t, i, a) in enumerate(rhs_rows):
             if t == 0 and i == j and a == c:
                 rhs[c, k] = 1.0
-    U, S, Vt = np.linalg.svd(Z, full_matrices=False)
+    try:
+        U, S, Vt = np.linalg.svd(Z, full_matrices=False)
+    except np.linalg.LinAlgError:
+        # LAPACK's divide-and-conquer driver (gesdd) gives up on a few
+        # matrices; the QR-iteration driver computes the same decomposition
+        import scipy.linalg
+        U, S, Vt = scipy.linalg.svd(Z, full_matrices=False, lapack_driver="gesvd")
     rank = int(np.sum(S > rtol * S[0]))
     Zp = (Vt[:rank].T / S[:rank]) @ U[:, :rank].T          # Z^+
     P = np.eye(D) - Zp @ Z
