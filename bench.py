@@ -35,15 +35,12 @@ METRIC = "MPC steps/s & ADMM iters/s, batched+warm-start vs plain at 1e-4 rel; H
 UNIT = "MPC steps/s"
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_sweep.cu")
-# DRAM bytes (read + write) of one sweep_kernel launch of a workload from an
-# ncu capture, and the sha256 of the kernel source it was taken on; reported
-# as null for other workloads and when the source has changed since.
-NCU_TRAFFIC = {"workload": "chain1024", "src_sha256": "82fb4a1ebcf2a59f25bf54a70c1e95e4fb0e1907e249160eb066d13d18dfed25",
-               "bytes_per_launch": 158949632,  # profiles/sweep_kernel_chain1024.md
-               # the same kernel's on-chip load from the full capture (50 fixed
-               # iterations, same launch shape): where the loop's bytes are served
-               "onchip": {"lts_throughput_pct_of_peak": 21.9, "l2_hit_rate_pct": 93.6,
-                          "issue_active_pct": 38.3, "dram_throughput_pct_of_peak": 1.6}}
+# Counters of one sweep_kernel launch per workload from ncu captures of the
+# kernel source whose sha256 is given (the capture commands are recorded with
+# the profile summaries): DRAM bytes read + written, the iterations that
+# launch ran, and the on-chip figures of the same kernel.  A workload without
+# a capture of the current source reports null.
+NCU = {"src_sha256": None, "workloads": {}}
 
 
 INNER_QP = {"box": "diagonal Q, R with boxes (closed-form row Phi-step)",
@@ -72,6 +69,17 @@ def bench_config(prob, world: int, inner_qp: str = "box", stale_prob: float = 0.
 
 def kernel_sha() -> str:
     return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+
+
+def ncu_record(workload_name: str, inner_qp: str, stale_prob: float) -> dict:
+    """`traffic` (DRAM bytes per launch, with the iterations of the captured
+    launch) and the on-chip counters from the ncu capture of this workload, if
+    it was taken on the current kernel source; null otherwise."""
+    w = NCU["workloads"].get(workload_name)
+    if w is None or NCU["src_sha256"] != kernel_sha() or inner_qp != "box" or stale_prob != 0:
+        return {"traffic": None, "onchip": None}
+    return {"traffic": w["dram_bytes_per_launch"], "traffic_launch_iters": w["iters_per_launch"],
+            "onchip": w.get("onchip")}
 
 
 def measured_peaks():
@@ -155,6 +163,88 @@ def replica_throughput(t_local: float, steps: int, world: int, dist=None, device
     return world * steps / t, t
 
 
+def closed_loop(solver, x0, K, warm, flush):
+    """K closed-loop MPC steps of every instance of `solver` from x0 (step 0
+    cold, the others `warm`): per step the library's CUDA-event times (sweep
+    kernel, whole step; the L2 flushed before each step outside the events)
+    and every instance's iterations and status."""
+    import torch
+    import paper_2103_14990_gb300 as pkg
+    x = x0.clone()
+    xn = torch.empty_like(x)
+    u = torch.empty(x.shape[0], solver.nu, device="cuda")
+    rec = {"kms": [], "sms": [], "iters": [], "status": []}
+    for tau in range(K):
+        if flush is not None:
+            flush.zero_()
+        rc, st = solver.step(x, u, xn, warm=(pkg.WARM_COLD if tau == 0 else warm), stats=True)
+        a, b = solver.timing()
+        rec["kms"].append(a)
+        rec["sms"].append(b)
+        rec["iters"].append([d["iters"] for d in st])
+        rec["status"].append([d["status"] for d in st])
+        x, xn = xn, x
+    rec["x_final"] = x
+    return rec
+
+
+def merge_records(recs):
+    """Records of several one-instance loops as one record of instance-steps
+    (times add up; iterations and status side by side)."""
+    out = {"kms": [], "sms": [], "iters": [], "status": []}
+    K = len(recs[0]["sms"])
+    for tau in range(K):
+        out["kms"].append(sum(r["kms"][tau] for r in recs))
+        out["sms"].append(sum(r["sms"][tau] for r in recs))
+        out["iters"].append([r["iters"][tau][0] for r in recs])
+        out["status"].append([r["status"][tau][0] for r in recs])
+    return out
+
+
+def summarise(rec, unit=UNIT):
+    """MPC steps/s (instance-steps over the summed whole-step event time),
+    ADMM iterations/s (instance iterations over the summed sweep-kernel time),
+    iterations per instance-step, steps stopped at max_iter, and the same
+    rates over the steps that converged."""
+    import numpy as np
+    K = len(rec["sms"])
+    it = np.array(rec["iters"], dtype=np.float64)
+    stt = np.array(rec["status"])
+    n_inst = it.shape[1]
+    s_step, s_kern = sum(rec["sms"]) / 1e3, sum(rec["kms"]) / 1e3
+    out = {"value": round(n_inst * K / s_step, 3), "unit": unit, "steps": K,
+           "ms_per_step": round(1e3 * s_step / K, 4),
+           "admm_iters_per_s": round(float(it.sum()) / s_kern, 1),
+           "iters_per_step": round(float(it.mean()), 2),
+           "steps_at_max_iter": int((stt != 0).sum())}
+    if n_inst > 1:
+        out["launch_iters_per_step"] = round(float(it.max(axis=1).mean()), 2)
+    else:
+        conv = [t for t in range(K) if rec["status"][t][0] == 0]
+        if conv:
+            cs = sum(rec["sms"][t] for t in conv) / 1e3
+            ck = sum(rec["kms"][t] for t in conv) / 1e3
+            ci = sum(rec["iters"][t][0] for t in conv)
+            out["converged_steps"] = {"steps": len(conv), "value": round(len(conv) / cs, 3), "unit": unit,
+                                      "admm_iters_per_s": round(ci / ck, 1),
+                                      "iters_per_step": round(ci / len(conv), 2)}
+    return out
+
+
+def alg_roofline(info, rec, peak, peak_src):
+    """HBM roofline of the sweep kernel by algorithmic bytes (every N_j once
+    per iteration, the exchanged row sums and the compact iterate): bytes of
+    the iterations run / sweep-kernel event time."""
+    iters = sum(max(i) for i in rec["iters"])
+    kern_s = sum(rec["kms"]) / 1e3
+    achieved = info["iter_bytes_min"] * iters / kern_s / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": peak_src,
+            "algorithmic_bytes_per_iter": info["iter_bytes_min"],
+            "kernel_load_bytes_per_iter": info["iter_bytes"],
+            "mean_launch_ms": round(1e3 * kern_s / len(rec["kms"]), 4)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -189,20 +279,8 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def loop(K, warm):
-        x = x0.clone()
-        xn = torch.empty_like(x)
-        u = torch.empty(n, nu, device="cuda")
-        kms, sms, iters, status = [], [], [], []
-        for tau in range(K):
-            flush.zero_()
-            rc, st = solver.step(x, u, xn, warm=(pkg.WARM_COLD if tau == 0 else warm), stats=True)
-            a, b = solver.timing()
-            kms.append(a)
-            sms.append(b)
-            iters.append(st[0]["iters"])
-            status.append(st[0]["status"])
-            x, xn = xn, x
-        return kms, sms, iters, status, x
+        r = closed_loop(solver, x0, K, warm, flush)
+        return r["kms"], r["sms"], [i[0] for i in r["iters"]], [s[0] for s in r["status"]], r["x_final"]
 
     def sync_all():
         torch.cuda.synchronize()
@@ -214,12 +292,15 @@ def run_ours(args):
     sync_all()
     with ClockSampler(local) as clk:
         wall0 = time.perf_counter()
-        kms, sms, iters, status, xK = loop(args.steps, pkg.WARM_PREVIOUS)
+        rec = closed_loop(solver, x0, args.steps, pkg.WARM_PREVIOUS, flush)
         sync_all()
         wall = time.perf_counter() - wall0
+    kms, sms = rec["kms"], rec["sms"]
+    iters, status = [i[0] for i in rec["iters"]], [s[0] for s in rec["status"]]
     value, t_dev = replica_throughput(sum(sms) / 1e3, args.steps, world, dist, device="cuda")
     kern_s = sum(kms) / 1e3
     tot_iters = sum(iters)
+    warm_summary = summarise(rec)
 
     # the same closed loop replayed from captured CUDA graphs (whole-step events)
     solver.set_option(pkg.OPT_GRAPH, 1)
@@ -229,9 +310,8 @@ def run_ours(args):
     graph = {"value": args.steps / (sum(gs) / 1e3), "unit": UNIT, "iters_per_step": sum(git) / len(git)}
 
     # plain: cold start at every step, same kernel
-    pk, ps, pit, pst, _ = loop(args.steps, pkg.WARM_COLD)
-    plain = {"value": args.steps / (sum(ps) / 1e3), "unit": UNIT,
-             "admm_iters_per_s": sum(pit) / (sum(pk) / 1e3), "iters_per_step": sum(pit) / len(pit)}
+    plain = summarise(closed_loop(solver, x0, args.steps, pkg.WARM_COLD, flush))
+    plain["start"] = "cold (zeros) at every step, one instance per launch"
 
     # ablation of the paper's GPU mappings (Sec. III): ADMM iterations/s from x(0)
     ablation = {}
@@ -248,8 +328,10 @@ def run_ours(args):
     learned = (learned_line(prob, args)
                if (not args.no_learned and rank == 0 and world == 1 and args.inner_qp == "box"
                    and args.stale_prob == 0) else None)
-    batched = (batched_line(prob, args, flush)
-               if (args.batch > 1 and args.stale_prob == 0 and rank == 0 and world == 1) else None)
+    other = rank == 0 and world == 1 and args.inner_qp == "box" and args.stale_prob == 0
+    batched = batch_line(args, flush) if (other and not args.no_batch) else None
+    configs = ({name: config_line(name, args, flush) for name in ("chain10", "grid64") if name != args.workload}
+               if (other and not args.no_configs) else None)
 
     # e2e: host (pinned) buffers through the C ABI, H2D and D2H inside the timed region
     xh = torch.empty(n, nx, dtype=torch.float32, pin_memory=True)
@@ -268,19 +350,9 @@ def run_ours(args):
 
     # roofline of the sweep kernel: algorithmic bytes / CUDA-event kernel time
     peak, peak_src = measured_peaks()
-    achieved = info["iter_bytes"] * tot_iters / kern_s / 1e9
-    ncu_current = (NCU_TRAFFIC["src_sha256"] == kernel_sha() and NCU_TRAFFIC["workload"] == args.workload
-                   and args.inner_qp == "box" and args.stale_prob == 0)
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if ncu_current else None
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": peak_src, "kernel": "sweep_kernel",
-                "algorithmic_bytes_per_iter": info["iter_bytes"],
-                "mean_launch_ms": round(sum(kms) / len(kms), 4),
-                "note": "the operators stay in shared memory and L2: DRAM moves `traffic` bytes per launch, "
-                        "far below the algorithmic bytes; the loop is bound by on-chip latency (onchip)",
-                "onchip": NCU_TRAFFIC["onchip"] if ncu_current else None}
-
+    roofline = alg_roofline(info, rec, peak, peak_src)
+    roofline["kernel"] = "sweep_kernel"
+    roofline.update(ncu_record(args.workload, args.inner_qp, args.stale_prob))
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_dev / args.steps, 4),
@@ -290,6 +362,7 @@ def run_ours(args):
         "admm_iters_per_s": round(tot_iters / kern_s, 1),
         "iters_per_step": round(tot_iters / args.steps, 2),
         "steps_at_max_iter": int(sum(1 for s in status if s != 0)),
+        "converged_steps": warm_summary.get("converged_steps"),
         "plain": plain,
         "e2e": e2e,
         "roofline": roofline,
@@ -297,6 +370,7 @@ def run_ours(args):
         "ablation": ablation,
         "learned": learned,
         "batched": batched,
+        "configs": configs,
         "sweep": {"group_threads": info["group_threads"], "groups_per_cta": info["groups_per_cta"],
                   "wave": info["wave"], "grid_ctas": info["grid_ctas"], "smem_bytes": info["smem_bytes"],
                   "resident_n_items": info["resident_n_items"],
@@ -316,44 +390,99 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def batched_line(prob, args, flush):
-    """Several instances of the workload (the same plant, different x(0)) in
-    one context: one launch per MPC step advances every instance's closed
-    loop, an instance at rest once its ADMM has converged.  Instance-steps per
-    second against the single-instance line."""
+def config_line(name, args, flush):
+    """Another workload's closed loop on its own: the autotuned launch, warm
+    (previous step) against plain (cold) starts, the same number of steps."""
     import numpy as np
     import torch
-    import dataclasses
+    import paper_2103_14990_gb300 as pkg
+    prob = workload(name)
+    s = pkg.Solver([prob])
+    x0 = torch.tensor(prob.x0.astype(np.float32), device="cuda")
+    s.autotune(x0, iters=args.tune_iters)
+    s.set_option(pkg.OPT_TIMING, 1)
+    K = prob.mpc_steps
+    closed_loop(s, x0, args.warmup, pkg.WARM_PREVIOUS, flush)
+    warm = closed_loop(s, x0, K, pkg.WARM_PREVIOUS, flush)
+    plain = closed_loop(s, x0, K, pkg.WARM_COLD, flush)
+    info = s.info()
+    peak, peak_src = measured_peaks()
+    out = {"workload": prob.name, "steps": K, "warm": summarise(warm), "plain": summarise(plain),
+           "roofline": {**alg_roofline(info, warm, peak, peak_src), **ncu_record(name, "box", 0.0)},
+           "sweep": {"group_threads": info["group_threads"], "groups_per_cta": info["groups_per_cta"],
+                     "wave": info["wave"], "resident_n_items": info["resident_n_items"]}}
+    s.close()
+    return out
+
+
+def batch_line(args, flush):
+    """The mixed batch of independent instances (chain or grid per seed, N in
+    16..512, T in 5..15, d in 1..3, boxes): every instance's closed loop from
+    its x(0) for the same steps, at the same eps, in four forms --
+    batched: all instances in one context, one launch per MPC step (an
+    instance rests once its ADMM has converged), warm or cold starts;
+    single: one context per instance, one launch per instance per MPC step
+    (the plain one-instance form), cold or warm starts.
+    Rates are instance MPC steps per second of summed whole-step event time.
+    A fixed-iteration launch of the batch (all instances active) gives the
+    HBM roofline per ADMM iteration."""
+    import numpy as np
+    import torch
     import paper_2103_14990_gb300 as pkg
     from paper_2103_14990_gb300 import instances as I
-    B = args.batch
-    x0s = I.random_x0(prob.n_sub, B, seed=3000)
-    probs = [dataclasses.replace(prob, x0=x0s[b]) for b in range(B)]
-    s = pkg.Solver(probs)
-    x = torch.tensor(np.concatenate([p.x0 for p in probs]).astype(np.float32), device="cuda")
-    s.autotune(x, iters=args.tune_iters)
-    s.set_option(pkg.OPT_TIMING, 1)
-    xn = torch.empty_like(x)
-    u = torch.empty(x.shape[0], prob.nu, device="cuda")
-    steps = max(3, args.steps // 5)
-    ms, iters = 0.0, []
-    for tau in range(args.warmup + steps):
-        flush.zero_()
-        rc, st = s.step(x, u, xn, warm=(pkg.WARM_COLD if tau == 0 else pkg.WARM_PREVIOUS), stats=True)
-        if tau >= args.warmup:
-            ms += s.timing()[1]
-            iters.append([d["iters"] for d in st])
-        x, xn = xn, x
-    info = s.info()
-    s.close()
-    it = np.array(iters)
-    return {"instances": B, "steps": steps, "value": round(B * steps / (ms / 1e3), 3), "unit": "instance MPC steps/s",
-            "ms_per_step": round(ms / steps, 4), "launch_iters_per_step": round(float(it.max(axis=1).mean()), 2),
-            "instance_admm_iters_per_s": round(float(it.sum()) / (ms / 1e3), 1),
-            "instance_iters_per_step": round(float(it.mean()), 2),
-            "sweep": {"group_threads": info["group_threads"], "groups_per_cta": info["groups_per_cta"],
-                      "wave": info["wave"], "resident_n_items": info["resident_n_items"]},
-            "x0": "U[-0.9, 0.9] per instance (seed 3000); closed loops from x(0), warm start from the previous step"}
+    probs = I.batch256(args.batch_count)
+    K = args.batch_steps
+    t0 = time.time()
+    sb = pkg.Solver(probs)
+    torch.cuda.synchronize()
+    t_setup_b = time.time() - t0
+    xb = torch.tensor(np.concatenate([p.x0 for p in probs]).astype(np.float32), device="cuda")
+    sb.autotune(xb, iters=10)
+    sb.set_option(pkg.OPT_TIMING, 1)
+    closed_loop(sb, xb, 1, pkg.WARM_COLD, flush)                   # warm-up
+    w0 = time.perf_counter()
+    bw = closed_loop(sb, xb, K, pkg.WARM_PREVIOUS, flush)
+    wall_bw = time.perf_counter() - w0
+    bc = closed_loop(sb, xb, K, pkg.WARM_COLD, flush)
+    # per-iteration roofline: fixed iterations from x(0), every instance active
+    sb.set_option(pkg.OPT_FIXED_ITERS, 20)
+    fixed = closed_loop(sb, xb, 2, pkg.WARM_COLD, flush)
+    fixed = {k: v[1:] for k, v in fixed.items() if k != "x_final"}
+    sb.set_option(pkg.OPT_FIXED_ITERS, 0)
+    info = sb.info()
+    sb.close()
+    t0 = time.time()
+    singles = [pkg.Solver([p]) for p in probs]
+    torch.cuda.synchronize()
+    t_setup_s = time.time() - t0
+    for s in singles:
+        s.set_option(pkg.OPT_TIMING, 1)
+    xs = [torch.tensor(p.x0.astype(np.float32), device="cuda") for p in probs]
+    for s, x in zip(singles, xs):
+        closed_loop(s, x, 1, pkg.WARM_COLD, flush)                  # warm-up
+    w0 = time.perf_counter()
+    sc = merge_records([closed_loop(s, x, K, pkg.WARM_COLD, flush) for s, x in zip(singles, xs)])
+    wall_sc = time.perf_counter() - w0
+    sw = merge_records([closed_loop(s, x, K, pkg.WARM_PREVIOUS, flush) for s, x in zip(singles, xs)])
+    for s in singles:
+        s.close()
+    unit = "instance MPC steps/s"
+    out = {"instances": len(probs), "steps": K, "n_sub_total": info["n_sub_total"],
+           "batched_warm": summarise(bw, unit), "batched_cold": summarise(bc, unit),
+           "plain": summarise(sc, unit), "single_warm": summarise(sw, unit),
+           "wall_s": {"batched_warm": round(wall_bw, 3), "plain": round(wall_sc, 3)},
+           "setup_precompute_s": {"batched": round(t_setup_b, 2), "single_contexts": round(t_setup_s, 2)}}
+    out["speedup_batched_warm_vs_plain"] = round(out["batched_warm"]["value"] / out["plain"]["value"], 3)
+    out["speedup_batched_cold_vs_plain"] = round(out["batched_cold"]["value"] / out["plain"]["value"], 3)
+    peak, peak_src = measured_peaks()
+    out["roofline"] = {**alg_roofline(info, fixed, peak, peak_src), "iters_per_launch": 20,
+                       **ncu_record("batch256", "box", 0.0)}
+    out["sweep"] = {"group_threads": info["group_threads"], "groups_per_cta": info["groups_per_cta"],
+                    "wave": info["wave"], "resident_n_items": info["resident_n_items"]}
+    out["note"] = ("plain = one context per instance, one launch per instance per MPC step, cold starts; "
+                   "every form stops on the same Conv at eps 1e-4 (max_iter 1000); x(0) ~ U[-0.9, 0.9] per "
+                   "instance (seed = index)")
+    return out
 
 
 def learned_line(prob, args):
@@ -609,7 +738,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--batch", type=int, default=8, help="instances of the batched line (1: none)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the mixed-batch comparison")
+    ap.add_argument("--batch-count", type=int, default=256, help="instances of the mixed batch")
+    ap.add_argument("--batch-steps", type=int, default=10, help="closed-loop MPC steps of the mixed batch")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads' lines")
     ap.add_argument("--learn-replicas", type=int, default=8)
     ap.add_argument("--learn-steps", type=int, default=36)
     ap.add_argument("--learn-epochs", type=int, default=40)

@@ -49,6 +49,8 @@ extern "C" {
 #define DLMPC_ERR_TIMEOUT (-4)           /* a device-side wait gave up (bounded spin) */
 #define DLMPC_ERR_CUDA (-5)              /* a CUDA runtime call failed */
 #define DLMPC_ERR_NOMEM (-6)             /* device allocation failed */
+#define DLMPC_ERR_CAPACITY (-7)          /* an output buffer is smaller than the result; the
+                                            sizes needed are reported beside it */
 
 #define DLMPC_WARM_COLD 0      /* Psi = Lambda = 0 */
 #define DLMPC_WARM_PREVIOUS 1  /* continue from the state left by the previous step/set_state */
@@ -122,10 +124,14 @@ typedef struct {
   int32_t group_threads, groups_per_cta, wave; /* sweep shape (DLMPC_OPT_SWEEP_SHAPE) */
   int32_t resident_n_items;     /* patches whose N_j stays in shared memory for the whole step */
   int32_t resident_state_items; /* patches whose Psi, Lambda and q stay in shared memory */
-  int64_t iter_bytes;       /* algorithmic bytes of one compact ADMM iteration over all
-                               patches: N_j and N_j^T read once each, row partial sums
-                               read (|Patch(m)| per patch row) and written, the compact
-                               iterate (lhat, R, Y) read and written */
+  int64_t iter_bytes;       /* bytes the sweep kernel's own loads move in one compact ADMM
+                               iteration over all patches: N_j and its stored transpose
+                               N_j^T read once each, row partial sums read (|Patch(m)| per
+                               patch row) and written, the compact iterate (lhat, R, Y)
+                               read and written */
+  int64_t iter_bytes_min;   /* algorithmic bytes of the same iteration (the roofline's
+                               numerator): as iter_bytes with every N_j counted once (both
+                               products N_j^T alpha and N_j y read the same entries) */
 } dlmpc_info;
 
 /* Option keys for dlmpc_set_option. */
@@ -167,6 +173,11 @@ typedef struct {
                                      Psi-comp done once per patch instead of once per column);
                                      0: every iteration projects the stored Psi/Lambda.  Ignored
                                      (full form) while DLMPC_OPT_EXPORT_PHI is on. */
+#define DLMPC_OPT_PASS2 17        /* second product o = N_j y of a compact iteration (Psi-comp):
+                                     0 (default) reads the stored transpose N_j^T, 1 reads the
+                                     rows of N_j, the lines the first product N_j^T alpha has
+                                     just read (L2 hits when N_j streams from HBM); same result
+                                     up to FP32 summation order */
 
 /* Builds the locality structure (hop-distance BFS, Patch(j), rows of Z_AB that
  * touch each patch) for n_inst instances, copies all inputs to the device and
@@ -262,12 +273,17 @@ int dlmpc_get_timing(dlmpc_ctx *ctx, float *ms);
  * pointers owned by the caller; nothing is allocated.
  * Workspace: one static device array of DLMPC_NOALLOC_MAX_DOUBLES doubles
  * (8 MiB), held by every GPU that loads the library until the process exits.
- * A block needing more than that (D*m + (3+nrhs)*m + 8*D + m/2 + 1 doubles)
- * or nrhs > 32 returns DLMPC_ERR_ARG without launching anything.  The array's
- * device address is looked up on the first call on each device, with that
- * device current; make that first call before any stream capture.  Every call
- * uses the same array: calls that overlap on the GPU race, so serialise them.
- * Asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream). */
+ * A block needing more than that (D*m + (3+nrhs)*m + 8*D + (m+1)/2 doubles,
+ * integer division) or nrhs > 32 returns DLMPC_ERR_ARG without launching
+ * anything.  The array's device address is looked up on the first call on
+ * each device, with that device current; make that first call before any
+ * stream capture.  Every call uses the same array: calls that overlap on the
+ * GPU race, so serialise them.
+ * Runs on `stream` (a cudaStream_t, NULL = legacy default stream) and waits
+ * for it: the call reads {rank, nullity} back (8 bytes into host stack
+ * memory) and returns DLMPC_ERR_CAPACITY when nullity > k_cap, in which case
+ * N_dev holds the first k_cap basis columns and rank_nullity_dev the true
+ * sizes; DLMPC_ERR_CUDA if the launch or the wait fails. */
 #define DLMPC_NOALLOC_MAX_DOUBLES (1 << 20)
 int dlmpc_factor_patch_noalloc(const double *Z_dev, int32_t m, int32_t D, const double *rhs_dev,
                                int32_t nrhs, double *N_dev, int32_t k_cap, double *q_dev,

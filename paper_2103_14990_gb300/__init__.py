@@ -24,6 +24,7 @@ DLMPC_ERR_NONFINITE = -3
 DLMPC_ERR_TIMEOUT = -4
 DLMPC_ERR_CUDA = -5
 DLMPC_ERR_NOMEM = -6
+DLMPC_ERR_CAPACITY = -7
 DLMPC_MAX_COUPLED = 4      # coupled rows per subsystem and slot kind
 DLMPC_MAX_REGIONS = 1024   # explicit-solution regions per subsystem and slot kind
 
@@ -46,6 +47,7 @@ OPT_COMPACT = 13
 OPT_BLOCK_PHI = 14
 OPT_STALE_PROB = 15
 OPT_STALE_SEED = 16
+OPT_PASS2 = 17
 
 # Every entry point declared in include/dlmpc.h (checked by the tests).
 EXPORTED = [
@@ -96,7 +98,7 @@ class Info_C(ctypes.Structure):
                 ("threads_per_cta", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
                 ("group_threads", ctypes.c_int32), ("groups_per_cta", ctypes.c_int32), ("wave", ctypes.c_int32),
                 ("resident_n_items", ctypes.c_int32), ("resident_state_items", ctypes.c_int32),
-                ("iter_bytes", ctypes.c_int64)]
+                ("iter_bytes", ctypes.c_int64), ("iter_bytes_min", ctypes.c_int64)]
 
 
 _LIB = None

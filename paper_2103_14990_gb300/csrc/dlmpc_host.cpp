@@ -146,6 +146,7 @@ struct dlmpc_ctx {
   int64_t resident_n_items = 0, resident_state_items = 0;
   int residency = 2;  // 0: nothing resident, 1: compact iterate, Psi/Lambda and q resident, 2: also N
   int compact = 1;    // iterations after the first of a launch on the compact iterate
+  int pass2_rows = 0; // DLMPC_OPT_PASS2
   bool block_cost = false;  // some instance has full cost blocks: slot box-QP Phi-step
   // Explicit solution of the slot QP with coupled rows (some instance has any):
   // per key 2 * global subsystem + kind (0 state, 1 input) the first region and
@@ -196,10 +197,12 @@ struct dlmpc_ctx {
     bool phi, trace;
     int compact, block;
     unsigned long long stale_thr, stale_seed;
+    int pass2_rows;
     bool operator==(const GraphKey &o) const {
       return x == o.x && u == o.u && xn == o.xn && warm == o.warm && stats == o.stats && plan == o.plan &&
              fixed == o.fixed && max_iter == o.max_iter && phi == o.phi && trace == o.trace && compact == o.compact &&
-             block == o.block && stale_thr == o.stale_thr && stale_seed == o.stale_seed;
+             block == o.block && stale_thr == o.stale_thr && stale_seed == o.stale_seed &&
+             pass2_rows == o.pass2_rows;
     }
   };
   struct GraphEntry {
@@ -1286,6 +1289,7 @@ Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_d
   P.trace = ctx->trace ? ctx->d_trace.p : nullptr;
   P.skip_arrival_cta = ctx->skip_arrival_cta;
   P.compact = ctx->compact;
+  P.pass2_rows = ctx->pass2_rows;
   P.stale_thr = ctx->stale_thr;
   P.stale_seed = ctx->stale_seed;
   P.block_cost = (ctx->block_cost || ctx->force_block) ? 1 : 0;
@@ -1330,7 +1334,7 @@ int enqueue_step(dlmpc_ctx *ctx, const Params &P, bool with_stats, bool events, 
 int graph_step(dlmpc_ctx *ctx, const Params &P, bool with_stats) {
   dlmpc_ctx::GraphKey key{P.x, P.u, P.x_next, P.warm, with_stats, ctx->plan_version, P.fixed_iters, P.max_iter,
                           P.Phi != nullptr, P.trace != nullptr, P.compact, P.block_cost, P.stale_thr,
-                          P.stale_seed};
+                          P.stale_seed, P.pass2_rows};
   for (auto &ge : ctx->graphs)
     if (ge.key == key) {
       CK(cudaGraphLaunch(ge.exec, ctx->stream), "cudaGraphLaunch");
@@ -1596,6 +1600,10 @@ extern "C" int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value) {
     case DLMPC_OPT_LEARN_PLANT: ctx->learn_plant = value != 0; return 0;
     case DLMPC_OPT_TEST_SKIP_ARRIVAL: ctx->skip_arrival_cta = (int)value; return 0;
     case DLMPC_OPT_COMPACT: ctx->compact = value != 0; return 0;
+    case DLMPC_OPT_PASS2:
+      if (value != 0 && value != 1) return ctx->fail(DLMPC_ERR_ARG, "DLMPC_OPT_PASS2 must be 0 or 1");
+      ctx->pass2_rows = (int)value;
+      return 0;
     case DLMPC_OPT_BLOCK_PHI: ctx->force_block = value != 0; return 0;
     case DLMPC_OPT_STALE_PROB:
       if (!(value >= 0 && value <= 1)) return ctx->fail(DLMPC_ERR_ARG, "the message-loss probability must lie in [0, 1]");
@@ -1659,15 +1667,16 @@ extern "C" int dlmpc_get_info(dlmpc_ctx *ctx, dlmpc_info *info) {
   // bytes one compact iteration must move per patch: N_j and N_j^T read once
   // each, the row sums of every patch row read, the patch's own row sums
   // written, lhat and R read and written, Y read and written
-  int64_t bytes = 0;
+  int64_t bytes = 0, nbytes = 0;
   for (const Item &it : ctx->items) {
     const int64_t dcol = (int64_t)it.r_sub * it.n_mem;
-    bytes += 2LL * it.dred * it.k * 4;               // N_j, N_j^T
+    nbytes += (int64_t)it.dred * it.k * 4;           // N_j (its transpose holds the same entries)
     for (int e = 0; e < it.n_mem; ++e) bytes += (int64_t)ctx->np_of[ctx->members[it.mem_off + e]] * it.r_sub * 4;
     bytes += dcol * 4;                               // row partial sums written
     bytes += 2LL * (dcol + it.dred + it.k) * 4;      // lhat, R, Y
   }
-  info->iter_bytes = bytes;
+  info->iter_bytes = bytes + 2 * nbytes;
+  info->iter_bytes_min = bytes + nbytes;
   return 0;
 }
 

@@ -14,7 +14,9 @@
 // device, with that device current) and cached; that first call must therefore
 // come before any stream capture.  All calls share the array: calls that
 // overlap on the GPU (different streams, or different host threads on one
-// device) race and must be serialised by the caller.
+// device) race and must be serialised by the caller.  Each call waits for its
+// kernel and reports a null space wider than the caller's N buffer
+// (DLMPC_ERR_CAPACITY) instead of cutting it silently.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -235,7 +237,16 @@ extern "C" int dlmpc_factor_patch_noalloc(const double *Z_dev, int32_t m, int32_
   if (need > DLMPC_NOALLOC_MAX_DOUBLES) return DLMPC_ERR_ARG;  // block too large for the static workspace
   double *ws = nullptr;
   if (scratch_for_current_device(&ws) != cudaSuccess) return DLMPC_ERR_CUDA;
-  factor_dense_noalloc_kernel<<<1, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
-      Z_dev, m, D, rhs_dev, nrhs, N_dev, k_cap, q_dev, rank_nullity_dev, feas_dev, ws);
-  return cudaGetLastError() == cudaSuccess ? DLMPC_OK : DLMPC_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  factor_dense_noalloc_kernel<<<1, kThreads, 0, st>>>(Z_dev, m, D, rhs_dev, nrhs, N_dev, k_cap, q_dev,
+                                                      rank_nullity_dev, feas_dev, ws);
+  if (cudaGetLastError() != cudaSuccess) return DLMPC_ERR_CUDA;
+  // the nullity is known only once the factorisation has run: read it back
+  // (host stack memory, no allocation) so that a basis wider than N_dev is
+  // reported instead of silently cut
+  int32_t rn[2] = {0, 0};
+  if (cudaMemcpyAsync(rn, rank_nullity_dev, sizeof(rn), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return DLMPC_ERR_CUDA;
+  return rn[1] > k_cap ? DLMPC_ERR_CAPACITY : DLMPC_OK;
 }

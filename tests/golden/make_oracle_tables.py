@@ -2,9 +2,10 @@
 
 Per-MPC-step ADMM iteration counts (and u norms) of the 50-step closed loop
 of the N=1024 chain (T=10, d=3, boxes, seed 0), for a cold start at every step
-and for a start from the previous step's Psi and Lambda.  The benchmark's CPU
+and for a start from the previous step's Psi and Lambda, and the closed-loop
+states x(tau) at tau = 16, 20, 30 of both loops.  The benchmark's CPU
 baseline and reference arm time bounded samples of oracle iterations and scale
-them by these counts.  Run: python tests/golden/make_oracle_tables.py
+them by these counts; the full-size parity tests start from those states.  Run: python tests/golden/make_oracle_tables.py
 """
 import json
 import multiprocessing as mp
@@ -24,7 +25,11 @@ def run(warm):
     o = O.Oracle(p)
     t0 = time.time()
     xs, us, its, stats = o.run_mpc(p.mpc_steps, warm=warm)
+    keep = [16, 20, 30]
     return warm, {"iters": [int(i) for i in its],
+                  # closed-loop states x(tau) of this loop at a few steps after
+                  # the steps that cannot meet the state box (parity inputs)
+                  "x_at": {str(t): [float(v) for v in xs[t].reshape(-1)] for t in keep},
                   "status": [int(s.status) for s in stats],
                   "r_max": [float(s.r_max) for s in stats],
                   "u_norm": [float(np.linalg.norm(u)) for u in us],

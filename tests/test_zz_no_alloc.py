@@ -69,3 +69,72 @@ def test_noalloc_rejects_blocks_above_the_static_workspace():
     a = vp(dummy.data_ptr())
     rc = lib.dlmpc_factor_patch_noalloc(a, m, D, a, 2, a, 8, a, a, a, None)
     assert rc == pkg.DLMPC_ERR_ARG
+
+
+def _dup_row_block():
+    """An interior chain patch block with its first row appended again (same
+    right-hand side): the rank drops by one against the row count."""
+    p = I.make_instance(16, 10, 3, seed=1, boxes=True)
+    blk = O.column_block(p, 7)
+    Z = np.vstack([blk.Z, blk.Z[:1]])
+    rhs = np.hstack([blk.rhs, blk.rhs[:, :1]])
+    return Z, rhs
+
+
+def test_noalloc_duplicated_row_rank_and_projector():
+    """rank = the rank of Z (one less than its rows), feas ~ 0, and the
+    projector N N^T equal to the one of scipy's SVD null space."""
+    import scipy.linalg
+    import torch
+    import paper_2103_14990_gb300 as pkg
+    lib = pkg.load_library()
+    Z, rhs = _dup_row_block()
+    m, D = Z.shape
+    r_ref = np.linalg.matrix_rank(Z)
+    assert r_ref < m
+    Nn = scipy.linalg.null_space(Z)
+    for _ in range(2):                              # two calls in a row on the shared workspace
+        rc, N, q, rn, feas = _call(lib, torch, Z, rhs, D)
+        assert rc == 0
+        assert int(rn[0]) == r_ref and int(rn[1]) == D - r_ref == Nn.shape[1]
+        k = int(rn[1])
+        assert feas < 1e-9
+        assert np.max(np.abs(N[:, :k] @ N[:, :k].T - Nn @ Nn.T)) < TOL
+        assert np.all(N[:, k:] == 0.0)
+        q_ref = np.linalg.lstsq(Z, rhs.T, rcond=None)[0].T          # min-norm solutions
+        assert np.max(np.abs(q - q_ref)) < TOL
+
+
+def test_noalloc_inconsistent_rhs_reports_infeasibility():
+    """The duplicated row with a different right-hand side has no solution:
+    feas (max |Z q - rhs|) is reported well above zero."""
+    import torch
+    import paper_2103_14990_gb300 as pkg
+    lib = pkg.load_library()
+    Z, rhs = _dup_row_block()
+    rhs = rhs.copy()
+    rhs[:, -1] = rhs[:, 0] + 1.0                    # row m-1 repeats row 0 with another value
+    rc, N, q, rn, feas = _call(lib, torch, Z, rhs, Z.shape[1])
+    assert rc == 0
+    assert feas > 0.1
+
+
+def test_noalloc_null_space_wider_than_the_buffer():
+    """k_cap below the nullity: DLMPC_ERR_CAPACITY, the true sizes in
+    rank_nullity, and only the first k_cap columns written, each a unit vector
+    of the null space."""
+    import torch
+    import paper_2103_14990_gb300 as pkg
+    lib = pkg.load_library()
+    p = I.make_instance(16, 10, 3, seed=1, boxes=True)
+    blk = O.column_block(p, 7)
+    D = blk.Z.shape[1]
+    k_true = D - blk.rank
+    k_cap = k_true - 5
+    rc, N, q, rn, feas = _call(lib, torch, blk.Z, blk.rhs, k_cap)
+    assert rc == pkg.DLMPC_ERR_CAPACITY
+    assert int(rn[1]) == k_true and int(rn[0]) == blk.rank
+    assert N.shape == (D, k_cap)
+    assert np.allclose(N.T @ N, np.eye(k_cap), atol=1e-10)
+    assert np.max(np.abs(blk.Z @ N)) < 1e-10
+    assert feas < 1e-9
