@@ -173,11 +173,6 @@ typedef struct {
                                      Psi-comp done once per patch instead of once per column);
                                      0: every iteration projects the stored Psi/Lambda.  Ignored
                                      (full form) while DLMPC_OPT_EXPORT_PHI is on. */
-#define DLMPC_OPT_PASS2 17        /* second product o = N_j y of a compact iteration (Psi-comp):
-                                     0 (default) reads the stored transpose N_j^T, 1 reads the
-                                     rows of N_j, the lines the first product N_j^T alpha has
-                                     just read (L2 hits when N_j streams from HBM); same result
-                                     up to FP32 summation order */
 
 /* Builds the locality structure (hop-distance BFS, Patch(j), rows of Z_AB that
  * touch each patch) for n_inst instances, copies all inputs to the device and
@@ -192,6 +187,27 @@ int dlmpc_setup(const dlmpc_problem *probs, int32_t n_inst, void *stream, dlmpc_
  * offsets q_c = Z_j^+ e_c (stored FP32).  Returns DLMPC_ERR_INFEASIBLE_LOCALITY
  * if max_c ||Z_j q_c - e_c|| exceeds 1e-9 for some j. Synchronous. */
 int dlmpc_precompute(dlmpc_ctx *ctx);
+
+/* Plant update in place (Sec. IV-C: the precomputation dominates the GPU time
+ * at large N, and Sec. V: a model that changes while the network runs).
+ * n_changed subsystems (global indices over the context's instances, each at
+ * most once) get new rows of the dynamics: A_diag (n_changed x nx x nx, the
+ * new A_ii in the order of `subsystems`), A_off (for each changed subsystem
+ * in that order, the nx x nx blocks A_ij of its adjacency entries in CSR
+ * order; may be NULL when none has neighbours) and B (n_changed x nx x nu).
+ * The coupling graph, costs and bounds stay.  Only the column patches whose
+ * constraint rows see a changed subsystem (hop distance <= d + 1) are
+ * re-factorised, in FP64 as dlmpc_precompute, and their N_j, N_j^T and q_c
+ * replaced in place; all other operators, the iterates, options, launch plan
+ * and captured graphs stay valid, and the next steps use the new dynamics.
+ * All pointers are host pointers, copied.  Returns the number of patches
+ * re-factorised (>= 0); DLMPC_ERR_INFEASIBLE_LOCALITY when a patch's
+ * restricted constraint has no solution, DLMPC_ERR_ARG when a patch's
+ * null-space dimension changes (the operator layout is fixed at precompute:
+ * set up a new context for that plant) or for invalid arguments; on any
+ * error the context is left as it was.  Synchronous. */
+int dlmpc_update_plant(dlmpc_ctx *ctx, int32_t n_changed, const int32_t *subsystems, const double *A_diag,
+                       const double *A_off, const double *B);
 
 /* Checkpoint of the one-time precomputation (the paper has no counterpart):
  * dlmpc_export_operators writes every patch's null-space dimension, N_j, N_j^T

@@ -47,11 +47,10 @@ OPT_COMPACT = 13
 OPT_BLOCK_PHI = 14
 OPT_STALE_PROB = 15
 OPT_STALE_SEED = 16
-OPT_PASS2 = 17
 
 # Every entry point declared in include/dlmpc.h (checked by the tests).
 EXPORTED = [
-    "dlmpc_setup", "dlmpc_precompute", "dlmpc_step", "dlmpc_solve_batch", "dlmpc_step_host",
+    "dlmpc_setup", "dlmpc_precompute", "dlmpc_update_plant", "dlmpc_step", "dlmpc_solve_batch", "dlmpc_step_host",
     "dlmpc_set_option", "dlmpc_get_info", "dlmpc_get_state", "dlmpc_set_state",
     "dlmpc_get_patch", "dlmpc_get_operator", "dlmpc_get_timing", "dlmpc_get_trace", "dlmpc_last_error",
     "dlmpc_destroy", "dlmpc_autotune",
@@ -116,6 +115,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     vp, fp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)
     lib.dlmpc_setup.argtypes = [ctypes.POINTER(Problem_C), ctypes.c_int32, vp, ctypes.POINTER(vp)]
     lib.dlmpc_precompute.argtypes = [vp]
+    lib.dlmpc_update_plant.argtypes = [vp, ctypes.c_int32, _ip, _dp, _dp, _dp]
     lib.dlmpc_export_operators.argtypes = [vp, vp, ctypes.c_int64]
     lib.dlmpc_export_operators.restype = ctypes.c_int64
     lib.dlmpc_import_operators.argtypes = [vp, ctypes.c_void_p, ctypes.c_int64]
@@ -241,6 +241,18 @@ class Solver:
 
     def precompute(self):
         self._check(self.lib.dlmpc_precompute(self._ctx))
+
+    def update_plant(self, subsystems, A_diag, A_off, B) -> int:
+        """New A_ii, A_ij (CSR rows of the changed subsystems, concatenated)
+        and B_i for the listed global subsystems; re-factorises the patches
+        that see them.  Returns the number of patches re-factorised."""
+        sub = np.ascontiguousarray(subsystems, np.int32)
+        ad = np.ascontiguousarray(A_diag, np.float64)
+        ao = np.ascontiguousarray(A_off, np.float64) if A_off is not None and np.size(A_off) else None
+        bb = np.ascontiguousarray(B, np.float64)
+        return self._check(self.lib.dlmpc_update_plant(self._ctx, len(sub), _ptr(sub, ctypes.c_int32),
+                                                       _ptr(ad, ctypes.c_double), _ptr(ao, ctypes.c_double),
+                                                       _ptr(bb, ctypes.c_double)))
 
     def export_operators(self) -> bytes:
         """The precomputed operators as a blob (see dlmpc_import_operators)."""

@@ -137,6 +137,7 @@ struct dlmpc_ctx {
   std::vector<double> zval, rhs;
   std::vector<int64_t> rhs_off;
   std::vector<int32_t> kub;
+  bool z_stale = false;  // the plant changed since the arrays above were built
   bool precomputed = false;
   int max_dcol = 0, max_kpad = 4, max_dred_pad = 4, max_nmem = 1;
   int64_t n_floats = 0, q_floats = 0;
@@ -146,7 +147,6 @@ struct dlmpc_ctx {
   int64_t resident_n_items = 0, resident_state_items = 0;
   int residency = 2;  // 0: nothing resident, 1: compact iterate, Psi/Lambda and q resident, 2: also N
   int compact = 1;    // iterations after the first of a launch on the compact iterate
-  int pass2_rows = 0; // DLMPC_OPT_PASS2
   bool block_cost = false;  // some instance has full cost blocks: slot box-QP Phi-step
   // Explicit solution of the slot QP with coupled rows (some instance has any):
   // per key 2 * global subsystem + kind (0 state, 1 input) the first region and
@@ -197,12 +197,10 @@ struct dlmpc_ctx {
     bool phi, trace;
     int compact, block;
     unsigned long long stale_thr, stale_seed;
-    int pass2_rows;
     bool operator==(const GraphKey &o) const {
       return x == o.x && u == o.u && xn == o.xn && warm == o.warm && stats == o.stats && plan == o.plan &&
              fixed == o.fixed && max_iter == o.max_iter && phi == o.phi && trace == o.trace && compact == o.compact &&
-             block == o.block && stale_thr == o.stale_thr && stale_seed == o.stale_seed &&
-             pass2_rows == o.pass2_rows;
+             block == o.block && stale_thr == o.stale_thr && stale_seed == o.stale_seed;
     }
   };
   struct GraphEntry {
@@ -1087,6 +1085,24 @@ extern "C" int dlmpc_precompute(dlmpc_ctx *ctx) {
   if (!ctx) return DLMPC_ERR_ARG;
   const int nx = ctx->nx;
   cudaStream_t s = ctx->stream;
+  if (ctx->z_stale) {
+    // the plant was updated since setup: the reduced constraints again
+    ctx->zrow_ptr.clear();
+    ctx->zcol.clear();
+    ctx->zval.clear();
+    ctx->rhs.clear();
+    for (Item &it : ctx->items) {
+      const Instance &I = ctx->inst[it.inst];
+      it.z_off = (int64_t)ctx->zrow_ptr.size();
+      ctx->zrow_ptr.push_back((int64_t)ctx->zcol.size());
+      ctx->rhs_off[it.sub] = (int64_t)ctx->rhs.size();
+      const int m = build_reduced(I, ctx->nx, ctx->nu, it.sub - I.sub_off, ctx->zrow_ptr, ctx->zcol, ctx->zval,
+                                  ctx->rhs);
+      if (m < 0) return ctx->fail(DLMPC_ERR_INFEASIBLE_LOCALITY, "locality constraint infeasible");
+      it.mrows = m;
+    }
+    ctx->z_stale = false;
+  }
   int rc = upload_static(ctx);
   if (rc) return rc;
   // scratch layout for the factorisation: N with stride k_ub
@@ -1176,6 +1192,196 @@ extern "C" int dlmpc_precompute(dlmpc_ctx *ctx) {
   CK(launch_repack(d_scr.p, ctx->d_items.p, ctx->n_sub, d_Nscr.p, ctx->d_N.p, s), "repack_kernel");
   CK(cudaStreamSynchronize(s), "repack");
   return finish_precompute(ctx);
+}
+
+// Plant update (Sec. IV-C, Sec. V): new rows of A and B for a few
+// subsystems; only the patches that see them (their ring, d + 1 hops, holds a
+// changed subsystem) are re-factorised, into scratch first, so that a failed
+// update leaves the context as it was.
+extern "C" int dlmpc_update_plant(dlmpc_ctx *ctx, int32_t n_changed, const int32_t *subsystems,
+                                  const double *A_diag, const double *A_off, const double *B) {
+  NvtxRange range("dlmpc_update_plant");
+  if (!ctx) return DLMPC_ERR_ARG;
+  if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
+  if (n_changed < 1 || !subsystems || !A_diag || !B)
+    return ctx->fail(DLMPC_ERR_ARG, "dlmpc_update_plant: null argument or n_changed < 1");
+  const int nx = ctx->nx, nu = ctx->nu;
+  cudaStream_t s = ctx->stream;
+  // instance of every global subsystem
+  auto inst_of = [&](int g) {
+    int b = 0;
+    while (b + 1 < ctx->n_inst && ctx->inst[b + 1].sub_off <= g) ++b;
+    return b;
+  };
+  std::vector<char> seen(ctx->n_sub, 0);
+  int64_t off_entries = 0;
+  for (int c = 0; c < n_changed; ++c) {
+    const int g = subsystems[c];
+    if (g < 0 || g >= ctx->n_sub) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_update_plant: subsystem out of range");
+    if (seen[g]) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_update_plant: subsystem listed twice");
+    seen[g] = 1;
+    const Instance &I = ctx->inst[inst_of(g)];
+    const int i = g - I.sub_off;
+    off_entries += I.adj_ptr[i + 1] - I.adj_ptr[i];
+  }
+  if (off_entries > 0 && !A_off) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_update_plant: A_off is null");
+  for (int64_t e = 0; e < (int64_t)n_changed * nx * nx; ++e)
+    if (!std::isfinite(A_diag[e])) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_update_plant: non-finite A_diag");
+  for (int64_t e = 0; e < off_entries * nx * nx; ++e)
+    if (!std::isfinite(A_off[e])) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_update_plant: non-finite A_off");
+  for (int64_t e = 0; e < (int64_t)n_changed * nx * nu; ++e)
+    if (!std::isfinite(B[e])) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_update_plant: non-finite B");
+  // the new plant on copies of the affected instances (committed on success)
+  std::vector<Instance> fresh = ctx->inst;
+  std::vector<char> affected(ctx->n_sub, 0);
+  std::vector<int> dist, touched;
+  {
+    const double *ao = A_off;
+    for (int c = 0; c < n_changed; ++c) {
+      const int g = subsystems[c];
+      const int b = inst_of(g);
+      Instance &I = fresh[b];
+      const int i = g - I.sub_off;
+      std::copy(A_diag + (int64_t)c * nx * nx, A_diag + (int64_t)(c + 1) * nx * nx,
+                I.A_diag.begin() + (int64_t)i * nx * nx);
+      for (int e = I.adj_ptr[i]; e < I.adj_ptr[i + 1]; ++e, ao += nx * nx)
+        std::copy(ao, ao + nx * nx, I.A_off.begin() + (int64_t)e * nx * nx);
+      std::copy(B + (int64_t)c * nx * nu, B + (int64_t)(c + 1) * nx * nu, I.B.begin() + (int64_t)i * nx * nu);
+      // every patch whose ring holds i: its hop distance to i is at most d + 1
+      dist.assign(I.n_sub, -1);
+      touched.clear();
+      bfs(I, i, I.d + 1, dist, touched);
+      for (int j : touched) affected[I.sub_off + j] = 1;
+    }
+  }
+  std::vector<int32_t> ids;
+  for (int g = 0; g < ctx->n_sub; ++g)
+    if (affected[g]) ids.push_back(g);
+  const int na = (int)ids.size();
+  // reduced constraints of the affected patches under the new plant, and the
+  // scratch layout of their factorisation (N with stride k_ub, q compact)
+  std::vector<int64_t> zptr, rhs_off(na);
+  std::vector<int32_t> zcol;
+  std::vector<double> zval, rhs;
+  std::vector<Item> scr(na), dst(na);
+  int64_t noff = 0, qoff = 0, max_D = 1, max_m = 1;
+  for (int a = 0; a < na; ++a) {
+    const int g = ids[a];
+    const Item &it = ctx->items[g];
+    const Instance &I = fresh[it.inst];
+    Item sc = it;
+    sc.z_off = (int64_t)zptr.size();
+    zptr.push_back((int64_t)zcol.size());
+    rhs_off[a] = (int64_t)rhs.size();
+    const int m = build_reduced(I, nx, nu, g - I.sub_off, zptr, zcol, zval, rhs);
+    if (m < 0)
+      return ctx->fail(DLMPC_ERR_INFEASIBLE_LOCALITY,
+                       "dlmpc_update_plant: subsystem " + std::to_string(g) + ": locality constraint infeasible");
+    sc.mrows = m;
+    sc.k = ctx->kub[g];
+    sc.kpad = ctx->kub[g];
+    sc.n_off = noff;
+    noff += round_up((int64_t)sc.dred_pad * sc.kpad, 4);
+    sc.q_off = qoff;
+    qoff += (int64_t)nx * sc.dred_pad;
+    scr[a] = sc;
+    dst[a] = it;
+    max_D = std::max<int64_t>(max_D, sc.dred);
+    max_m = std::max<int64_t>(max_m, m);
+  }
+  DevBuf<Item> d_scr, d_dst;
+  DevBuf<float> d_Nscr, d_qscr;
+  DevBuf<int64_t> d_zptr, d_rhs_off;
+  DevBuf<int32_t> d_zcol, d_rank, d_null, d_order, d_next;
+  DevBuf<double> d_zval, d_rhs, d_ws, d_feas;
+  CK(upload(d_scr, scr, s), "upload items");
+  CK(upload(d_dst, dst, s), "upload items");
+  CK(d_Nscr.alloc(std::max<int64_t>(noff, 4)), "alloc N scratch");
+  CK(d_qscr.alloc(std::max<int64_t>(qoff, 4)), "alloc q scratch");
+  CK(upload(d_zptr, zptr, s), "upload Z");
+  CK(upload(d_zcol, zcol, s), "upload Z");
+  CK(upload(d_zval, zval, s), "upload Z");
+  CK(upload(d_rhs, rhs, s), "upload rhs");
+  CK(upload(d_rhs_off, rhs_off, s), "upload rhs");
+  CK(d_rank.alloc(na), "alloc");
+  CK(d_null.alloc(na), "alloc");
+  CK(d_feas.alloc(na), "alloc");
+  const int64_t ws_stride = round_up(max_D * max_m + (3 + nx) * max_m + 8 * max_D + max_m / 2 + 8, 32);
+  int dev = 0, sms = 1;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
+  std::vector<int32_t> order(na);
+  std::iota(order.begin(), order.end(), 0);
+  auto work = [&](int a) { return (double)scr[a].dred * (double)scr[a].mrows * (double)scr[a].mrows; };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+  const int conc = (int)std::min<int64_t>({(int64_t)na, (int64_t)sms * 4,
+                                           std::max<int64_t>(1, ((int64_t)8 << 30) / (ws_stride * 8))});
+  CK(d_ws.alloc((size_t)conc * ws_stride), "alloc factor workspace");
+  CK(upload(d_order, order, s), "upload factor queue");
+  CK(d_next.alloc(1), "alloc factor queue");
+  CK(cudaMemsetAsync(d_next.p, 0, sizeof(int32_t), s), "memset");
+  FactorParams fp{};
+  fp.items = d_scr.p;
+  fp.n_items = na;
+  fp.zrow_ptr = d_zptr.p;
+  fp.zcol = d_zcol.p;
+  fp.zval = d_zval.p;
+  fp.rhs = d_rhs.p;
+  fp.rhs_off = d_rhs_off.p;
+  fp.ws = d_ws.p;
+  fp.ws_stride = ws_stride;
+  fp.Nmat = d_Nscr.p;
+  fp.qvec = d_qscr.p;
+  fp.feas = d_feas.p;
+  fp.rank = d_rank.p;
+  fp.nullity = d_null.p;
+  fp.nx = nx;
+  fp.use_smem = 0;
+  fp.order = d_order.p;
+  fp.next = d_next.p;
+  CK(launch_factor(fp, conc, (size_t)max_D * 8, s), "factor_kernel");
+  std::vector<double> feas(na);
+  std::vector<int32_t> nul(na);
+  CK(cudaMemcpyAsync(feas.data(), d_feas.p, 8 * feas.size(), cudaMemcpyDeviceToHost, s), "D2H");
+  CK(cudaMemcpyAsync(nul.data(), d_null.p, 4 * nul.size(), cudaMemcpyDeviceToHost, s), "D2H");
+  CK(cudaStreamSynchronize(s), "factorisation");
+  for (int a = 0; a < na; ++a) {
+    const int g = ids[a];
+    if (!(feas[a] <= 1e-9)) {
+      char buf[200];
+      snprintf(buf, sizeof buf, "dlmpc_update_plant: subsystem %d: ||Z q - e|| = %.3e (locality infeasible)", g,
+               feas[a]);
+      return ctx->fail(DLMPC_ERR_INFEASIBLE_LOCALITY, buf);
+    }
+    if (nul[a] != ctx->items[g].k) {
+      char buf[200];
+      snprintf(buf, sizeof buf,
+               "dlmpc_update_plant: subsystem %d: null-space dimension %d, the operator layout has %d "
+               "(set up a new context for this plant)", g, nul[a], ctx->items[g].k);
+      return ctx->fail(DLMPC_ERR_ARG, buf);
+    }
+  }
+  // commit: N and N^T repacked in place, q copied, the plant on the host and
+  // on the device (dynamics, network inputs); the setup-time constraint
+  // arrays are rebuilt before any later dlmpc_precompute
+  CK(launch_repack(d_scr.p, d_dst.p, na, d_Nscr.p, ctx->d_N.p, s), "repack_kernel");
+  for (int a = 0; a < na; ++a)
+    CK(cudaMemcpyAsync(ctx->d_q.p + dst[a].q_off, d_qscr.p + scr[a].q_off, sizeof(float) * nx * dst[a].dred_pad,
+                       cudaMemcpyDeviceToDevice, s),
+       "copy q");
+  ctx->inst.swap(fresh);
+  ctx->z_stale = true;
+  int64_t ad = 0, ao = 0, bm = 0;
+  for (const Instance &I : ctx->inst) {
+    CK(cudaMemcpyAsync(ctx->d_Adiag.p + ad, I.A_diag.data(), I.A_diag.size() * 8, cudaMemcpyHostToDevice, s), "H2D A");
+    CK(cudaMemcpyAsync(ctx->d_Aoff.p + ao, I.A_off.data(), I.A_off.size() * 8, cudaMemcpyHostToDevice, s), "H2D A");
+    CK(cudaMemcpyAsync(ctx->d_B.p + bm, I.B.data(), I.B.size() * 8, cudaMemcpyHostToDevice, s), "H2D B");
+    ad += (int64_t)I.A_diag.size();
+    ao += (int64_t)I.A_off.size();
+    bm += (int64_t)I.B.size();
+  }
+  CK(cudaStreamSynchronize(s), "update plant");
+  return na;
 }
 
 namespace {
@@ -1289,7 +1495,6 @@ Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_d
   P.trace = ctx->trace ? ctx->d_trace.p : nullptr;
   P.skip_arrival_cta = ctx->skip_arrival_cta;
   P.compact = ctx->compact;
-  P.pass2_rows = ctx->pass2_rows;
   P.stale_thr = ctx->stale_thr;
   P.stale_seed = ctx->stale_seed;
   P.block_cost = (ctx->block_cost || ctx->force_block) ? 1 : 0;
@@ -1306,6 +1511,13 @@ Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_d
   P.crow_stride = ctx->crow_stride;
   P.cpst = ctx->d_cp.p;
   return P;
+}
+
+// Sets the sweep kernel's dynamic shared-memory limit to this context's plan.
+cudaError_t bind_sweep_smem(const dlmpc_ctx *ctx, bool blk) {
+  const void *fn = sweep_kernel_ptr(ctx->nx, ctx->gt, blk);
+  if (!fn) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem);
 }
 
 // Enqueues one step: counter resets, the sweep, and (with stats) the
@@ -1334,7 +1546,7 @@ int enqueue_step(dlmpc_ctx *ctx, const Params &P, bool with_stats, bool events, 
 int graph_step(dlmpc_ctx *ctx, const Params &P, bool with_stats) {
   dlmpc_ctx::GraphKey key{P.x, P.u, P.x_next, P.warm, with_stats, ctx->plan_version, P.fixed_iters, P.max_iter,
                           P.Phi != nullptr, P.trace != nullptr, P.compact, P.block_cost, P.stale_thr,
-                          P.stale_seed, P.pass2_rows};
+                          P.stale_seed};
   for (auto &ge : ctx->graphs)
     if (ge.key == key) {
       CK(cudaGraphLaunch(ge.exec, ctx->stream), "cudaGraphLaunch");
@@ -1396,6 +1608,9 @@ int run_step(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_dev, in
   }
   const Params P = make_params(ctx, x_dev, u_dev, xn_dev, warm);
   const bool with_stats = stats != nullptr;
+  // the dynamic shared-memory limit is an attribute of the kernel function,
+  // shared by every context: set this context's before its launch
+  CK(bind_sweep_smem(ctx, P.block_cost != 0), "smem attr");
   ctx->kernel_events = !ctx->use_graph && ctx->timing;
   int rc = ctx->use_graph ? graph_step(ctx, P, with_stats) : enqueue_step(ctx, P, with_stats, ctx->timing != 0, s);
   if (rc) return rc;
@@ -1600,10 +1815,6 @@ extern "C" int dlmpc_set_option(dlmpc_ctx *ctx, int32_t key, double value) {
     case DLMPC_OPT_LEARN_PLANT: ctx->learn_plant = value != 0; return 0;
     case DLMPC_OPT_TEST_SKIP_ARRIVAL: ctx->skip_arrival_cta = (int)value; return 0;
     case DLMPC_OPT_COMPACT: ctx->compact = value != 0; return 0;
-    case DLMPC_OPT_PASS2:
-      if (value != 0 && value != 1) return ctx->fail(DLMPC_ERR_ARG, "DLMPC_OPT_PASS2 must be 0 or 1");
-      ctx->pass2_rows = (int)value;
-      return 0;
     case DLMPC_OPT_BLOCK_PHI: ctx->force_block = value != 0; return 0;
     case DLMPC_OPT_STALE_PROB:
       if (!(value >= 0 && value <= 1)) return ctx->fail(DLMPC_ERR_ARG, "the message-loss probability must lie in [0, 1]");

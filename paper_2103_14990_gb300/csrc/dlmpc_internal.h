@@ -108,8 +108,6 @@ struct Params {
   int32_t skip_arrival_cta;   // test of the bounded waits: this CTA leaves before its first
                               // iteration barrier (-1 = none)
   int32_t compact;            // != 0: iterations after the first use the compact iterate
-  int32_t pass2_rows;         // != 0: the compact iteration's o = N y reads the rows of N (the
-                              // lines its first pass has just read); 0: the stored N^T
   // simulated lost messages: the row sums patch j sends to member m at the end
   // of iteration k are lost when SplitMix64 draw (k N + j) N + m of stale_seed,
   // shifted right by 11, is below stale_thr (0: none); the receiver keeps the

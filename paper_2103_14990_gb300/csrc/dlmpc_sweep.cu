@@ -688,50 +688,6 @@ __device__ __forceinline__ void apply_n(const float *Nb, const float *tv, const 
   }
 }
 
-// out[r] = sum_a N[r][a] y[a] for the rows of a row-major N (kpad floats per
-// row, 16-byte aligned rows, kpad = 4 mod 8 so that 16 rows read by a half
-// warp hit distinct shared-memory bank groups): 16 consecutive rows per half
-// warp, the two halves of a warp covering the two halves of the column groups
-// of the same rows (as apply_n), all of a lane's loads of a row in flight.
-// Reads the rows of N instead of the columns of a stored transpose, so a
-// streamed N_j is read from HBM once per iteration (the first pass brings its
-// lines into L2).
-template <int GT>
-__device__ __forceinline__ void row_pass(const float *Nb, const float *y, int rows, int kpad, float *out, int gt) {
-  constexpr int kWarps = GT / 32;
-  const int ncg = kpad >> 2;
-  const int lane = gt & 31, w = gt >> 5;
-  const int half = lane >> 4;
-  const int h0 = (ncg + 1) >> 1;
-  const int cg_begin = half ? h0 : 0, cg_end = half ? ncg : h0;
-  for (int base = w * 16; base < rows; base += kWarps * 16) {
-    const int r = base + (lane & 15);
-    float o = 0.f;
-    if (r < rows) {
-      const float *nrow = Nb + r * kpad;
-      for (int cg0 = cg_begin; cg0 < cg_end; cg0 += 8) {
-        float4 n4[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          n4[u] = (cg0 + u < cg_end) ? *reinterpret_cast<const float4 *>(nrow + 4 * (cg0 + u))
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (cg0 + u < cg_end) {
-            const float4 y4 = *reinterpret_cast<const float4 *>(y + 4 * (cg0 + u));
-            o = fmaf(n4[u].x, y4.x, o);
-            o = fmaf(n4[u].y, y4.y, o);
-            o = fmaf(n4[u].z, y4.z, o);
-            o = fmaf(n4[u].w, y4.w, o);
-          }
-        }
-      }
-    }
-    o += __shfl_xor_sync(0xffffffffu, o, 16);
-    if (r < rows && half == 0) out[r] = o;
-  }
-}
-
 // Conv of one patch from the per-thread squared residual partials (Sec. II-A
 // stopping rule, per subsystem): ||Phi - Psi||_F <= eps_p and
 // rho ||Psi - Psi_prev||_F <= eps_d.  GB300 runs FP64 at a small fraction of
@@ -978,12 +934,8 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
   group_sync(g, GT);
   if (tr) trace_point(P, iter, 7);
 
-  // pass 2: o = N y, by the rows of N (resident in shared memory, or the
-  // lines pass 1 has just read), or flat over the stored N^T
-  if (P.pass2_rows)
-    row_pass<GT>(Nb, G.t, dred, kpad, G.part, gt);
-  else
-    flat_pass<8>(NTb, k, dpad, G.t, G.part, gt, GT);
+  // pass 2: o = N y, flat over N^T (from L2 also for patches whose N is resident)
+  flat_pass<8>(NTb, k, dpad, G.t, G.part, gt, GT);
   group_sync(g, GT);
   if (tr) trace_point(P, iter, 6);
 
@@ -991,7 +943,7 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
   float prim_f = 0.f, dual_f = 0.f;
   {
     const int nrg = dpad >> 2;
-    const int QS = P.pass2_rows ? 1 : (GT >= nrg ? small_div(GT, nrg) : 1);
+    const int QS = GT >= nrg ? small_div(GT, nrg) : 1;
     for (int red = gt; red < dred; red += GT) {
       float o = 0.f;
       for (int q = 0; q < QS; ++q) o += G.part[q * dpad + red];

@@ -60,11 +60,11 @@ def main(argv=None) -> int:
         s.autotune(x, iters=5)
         info = s.info()
         print(json.dumps({"autotuned": {k: info[k] for k in ("group_threads", "groups_per_cta", "wave",
-                                                              "resident_n_items", "iter_bytes")}}))
+                                                              "resident_n_items", "iter_bytes_min")}}))
     for _ in range(a.steps):
         rc, st = s.step(x, u, xn, warm=pkg.WARM_COLD)
         ms = s.timing()[0]
-        gbs = s.info()["iter_bytes"] * a.iters / (ms * 1e-3) / 1e9
+        gbs = s.info()["iter_bytes_min"] * a.iters / (ms * 1e-3) / 1e9
         print(f"kernel {ms:.4f} ms  {1e3 * ms / a.iters:.2f} us/iteration  {gbs:.0f} GB/s algorithmic  "
               f"status {st[0]['status']}")
     if a.trace:
