@@ -27,13 +27,14 @@ def main(argv=None) -> int:
     ap.add_argument("--compact", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--trace", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=256, help="instances of the mixed batch")
     ap.add_argument("--inner-qp", default="box", choices=["box", "block", "coupled"],
                     help="block: full SPD cost blocks; coupled: also 2 coupled state rows per slot")
     a = ap.parse_args(argv)
     import torch
     import paper_2103_14990_gb300 as pkg
     from paper_2103_14990_gb300 import instances as I
-    probs = I.batch256() if a.workload == "batch256" else \
+    probs = I.batch256(a.batch_count) if a.workload == "batch256" else \
         [{"chain1024": I.chain1024, "chain10": I.chain10, "grid64": I.grid64}[a.workload]()]
     if a.inner_qp == "block":
         probs = [I.with_block_costs(q, seed=101) for q in probs]

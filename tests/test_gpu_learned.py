@@ -54,6 +54,43 @@ def test_gradients_match_oracle(small_net):
         assert relerr(G[name], G_64[name]) < 3e-2, name       # BF16 against exact
 
 
+def test_network_kernels_at_the_benchmark_sizes():
+    """The learned start's network on the N = 1024 chain: 1024 rows (one per
+    subsystem), 70 inputs (patch state and each member's plant blocks), two
+    hidden layers of 256 and 812 outputs (Phi rows and Lambda of a
+    subsystem): forward and gradients against the FP64 network oracle with
+    the same BF16 rounding points, and against exact arithmetic."""
+    import torch
+    import paper_2103_14990_gb300 as pkg
+    s = pkg.Solver([I.chain1024()])
+    s.set_option(pkg.OPT_LEARN_PLANT, 1)
+    d_in, d_out = s.learned_dims()
+    s.close()
+    assert (d_in, d_out) == (70, 812)
+    rng = np.random.default_rng(11)
+    mlp = pkg.MLP(d_in, 256, d_out, seed=12)
+    p = M.round_bf16(mlp.get_params()).astype(np.float32)
+    mlp.set_params(p)
+    x = M.round_bf16(rng.uniform(-1, 1, (1024, d_in))).astype(np.float32)
+    t = rng.normal(size=(1024, d_out)).astype(np.float32)
+    xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+    P = {k: v.astype(np.float64) for k, v in mlp.unpack(p).items()}
+    y = mlp.forward(xd).cpu().numpy()
+    y_bf, _ = M.forward(P, x, bf16=True)
+    y_64, _ = M.forward(P, x)
+    assert relerr(y, y_bf) < 2e-3
+    assert relerr(y, y_64) < 1e-2
+    g, loss = mlp.gradients(xd, td)
+    G = mlp.unpack(g)
+    l_bf, G_bf = M.loss_and_grads(P, x, t, bf16=True)
+    _, G_64 = M.loss_and_grads(P, x, t)
+    assert abs(loss - l_bf) / l_bf < 1e-4
+    for name in ["W1", "b1", "W2", "b2", "W3", "b3"]:
+        assert relerr(G[name], G_bf[name]) < 5e-3, name
+        assert relerr(G[name], G_64[name]) < 3e-2, name
+    mlp.close()
+
+
 def test_adamw_steps_match_oracle():
     """Three training steps: each GPU update against the oracle's AdamW applied
     to the GPU's own gradient of that step (isolates the optimiser kernel)."""
