@@ -55,6 +55,9 @@ extern "C" {
 #define DLMPC_WARM_COLD 0      /* Psi = Lambda = 0 */
 #define DLMPC_WARM_PREVIOUS 1  /* continue from the state left by the previous step/set_state */
 #define DLMPC_WARM_LEARNED 2   /* learned initial Phi rows and Lambda, then a Psi-step first */
+#define DLMPC_WARM_CONVERGED 3 /* per instance: the previous step's state if that step met Conv
+                                  (or the state came from dlmpc_set_state), zeros otherwise: a step
+                                  stopped at max_iter is a worse start than zeros */
 
 typedef struct dlmpc_ctx dlmpc_ctx;
 typedef struct dlmpc_mlp dlmpc_mlp;
@@ -248,7 +251,7 @@ int dlmpc_get_info(dlmpc_ctx *ctx, dlmpc_info *info);
  * floats each; any may be NULL).  phi needs DLMPC_OPT_EXPORT_PHI. */
 int dlmpc_get_state(dlmpc_ctx *ctx, float *phi_dev, float *psi_dev, float *lam_dev);
 /* Replaces Psi and Lambda (device pointers, same layout); used by
- * DLMPC_WARM_PREVIOUS on the next step. */
+ * DLMPC_WARM_PREVIOUS and DLMPC_WARM_CONVERGED on the next step. */
 int dlmpc_set_state(dlmpc_ctx *ctx, const float *psi_dev, const float *lam_dev);
 
 /* Host copy of Patch(j) of global subsystem j (members as global indices);

@@ -643,7 +643,9 @@ class Oracle:
                 fixed_iters: Optional[int] = None, max_iter: Optional[int] = None,
                 x_feed: Optional[np.ndarray] = None):
         """Closed loop of Alg. 1.  warm = "cold" restarts every ADMM from zeros,
-        "previous" starts from the previous MPC step's Psi and Lambda.
+        "previous" starts from the previous MPC step's Psi and Lambda,
+        "converged" does so only when that step met Conv (zeros after a step
+        stopped at max_iter).
         If x_feed [steps, n_sub, nx] is given, the MPC step tau solves from
         x_feed[tau] instead of the closed-loop state (per-step parity)."""
         x = (self.prob.x0 if x0 is None else x0).copy()
@@ -651,7 +653,7 @@ class Oracle:
         Psi = Lam = None
         for tau in range(steps):
             xt = x if x_feed is None else x_feed[tau]
-            if warm == "cold":
+            if warm == "cold" or (warm == "converged" and stats and stats[-1].status != STATUS_CONVERGED):
                 Psi = Lam = None
             res = admm(self.lay, self.blocks, xt, Psi0=Psi, Lam0=Lam,
                        fixed_iters=fixed_iters, max_iter=max_iter)

@@ -31,6 +31,7 @@ DLMPC_MAX_REGIONS = 1024   # explicit-solution regions per subsystem and slot ki
 WARM_COLD = 0
 WARM_PREVIOUS = 1
 WARM_LEARNED = 2
+WARM_CONVERGED = 3
 
 OPT_FIXED_ITERS = 1
 OPT_MAX_ITER = 2

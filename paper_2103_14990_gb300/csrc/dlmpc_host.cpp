@@ -168,7 +168,7 @@ struct dlmpc_ctx {
   // device
   DevBuf<Item> d_items;
   DevBuf<int32_t> d_members, d_rev, d_np, d_grp_ptr, d_grp_items, d_cta_inst_ptr, d_cta_inst, d_adj_ptr, d_adj_idx,
-      d_inst_iters, d_err, d_inst_item_ptr, d_sub_off;
+      d_inst_iters, d_conv_prev, d_err, d_inst_item_ptr, d_sub_off;
   DevBuf<int64_t> d_goff;
   DevBuf<float> d_qblk2, d_rblk2, d_crow, d_expl;
   DevBuf<int32_t> d_rg_base, d_rg_cnt, d_rw_base, d_rw_cnt;
@@ -779,6 +779,8 @@ int upload_static(dlmpc_ctx *ctx) {
   CK(ctx->d_bar.alloc(3), "alloc barrier");
   CK(ctx->d_notconv.alloc(3 * ctx->n_inst), "alloc conv");
   CK(ctx->d_inst_iters.alloc(ctx->n_inst), "alloc iters");
+  CK(ctx->d_conv_prev.alloc(ctx->n_inst), "alloc conv flags");
+  CK(cudaMemsetAsync(ctx->d_conv_prev.p, 0, sizeof(int32_t) * ctx->n_inst, s), "memset");
   CK(ctx->d_err.alloc(8), "alloc err");
   CK(ctx->d_stats.alloc(ctx->n_inst), "alloc stats");
   CK(ctx->d_x.alloc((size_t)ctx->n_sub * nx), "alloc staging");
@@ -1472,6 +1474,7 @@ Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_d
   P.bar = ctx->d_bar.p;
   P.notconv = ctx->d_notconv.p;
   P.inst_iters = ctx->d_inst_iters.p;
+  P.conv_prev = ctx->d_conv_prev.p;
   P.item_r = ctx->d_item_r.p;
   P.item_s = ctx->d_item_s.p;
   P.err = ctx->d_err.p;
@@ -1584,7 +1587,8 @@ namespace {
 int run_step(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_dev, int warm, dlmpc_stats *stats) {
   NvtxRange range(warm == DLMPC_WARM_LEARNED ? "dlmpc_step (learned start)" : "dlmpc_step");
   if (!ctx->precomputed) return ctx->fail(DLMPC_ERR_ARG, "dlmpc_precompute has not run");
-  if (warm != DLMPC_WARM_COLD && warm != DLMPC_WARM_PREVIOUS && warm != DLMPC_WARM_LEARNED)
+  if (warm != DLMPC_WARM_COLD && warm != DLMPC_WARM_PREVIOUS && warm != DLMPC_WARM_LEARNED &&
+      warm != DLMPC_WARM_CONVERGED)
     return ctx->fail(DLMPC_ERR_ARG, "unsupported warm-start mode");
   cudaStream_t s = ctx->stream;
   if (ctx->export_phi && ctx->d_phi.n != (size_t)ctx->state_floats) {
@@ -2028,6 +2032,11 @@ extern "C" int dlmpc_set_state(dlmpc_ctx *ctx, const float *psi_dev, const float
   const size_t bytes = (size_t)ctx->state_floats * 4;
   CK(cudaMemcpyAsync(ctx->d_psi.p, psi_dev, bytes, cudaMemcpyDeviceToDevice, s), "set Psi");
   CK(cudaMemcpyAsync(ctx->d_lam.p, lam_dev, bytes, cudaMemcpyDeviceToDevice, s), "set Lambda");
+  // a state set by the caller is a start DLMPC_WARM_CONVERGED keeps
+  const std::vector<int32_t> ones(ctx->n_inst, 1);
+  CK(cudaMemcpyAsync(ctx->d_conv_prev.p, ones.data(), sizeof(int32_t) * ctx->n_inst, cudaMemcpyHostToDevice, s),
+     "conv flags");
+  CK(cudaStreamSynchronize(s), "set state");
   return 0;
 }
 

@@ -90,6 +90,7 @@ struct Params {
   unsigned long long *bar;    // [3] barrier counters: arrivals (low 32 bits) + not-converged items (high 32)
   unsigned int *notconv;      // [3][n_inst] not-converged items per instance (used when n_inst > 1)
   int32_t *inst_iters;        // [n_inst]
+  int32_t *conv_prev;         // [n_inst] != 0: the instance's last step met Conv (DLMPC_WARM_CONVERGED)
   float *item_r, *item_s;     // [n_items]
   int32_t *err;               // [8]: code, cta, iteration, aux, iterations run
   int32_t max_iter;

@@ -1144,9 +1144,12 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
     float *psi_g = P.Psi + it.st_off, *lam_g = P.Lam + it.st_off;
     float *psi_p = it.st_sm >= 0 ? arena + it.st_sm : psi_g;
     float *lam_p = it.st_sm >= 0 ? arena + it.st_sm + NX * dcol : lam_g;
+    // start: zeros, or the state left by the previous step (with
+    // DLMPC_WARM_CONVERGED only where that step met Conv)
+    const bool warm_i = P.warm == DLMPC_WARM_PREVIOUS || (P.warm == DLMPC_WARM_CONVERGED && P.conv_prev[it.inst] != 0);
     for (int e = gt; e < NX * dcol; e += GT) {
-      const float ps = (P.warm == DLMPC_WARM_COLD) ? 0.f : psi_g[e];
-      const float lm = (P.warm == DLMPC_WARM_COLD) ? 0.f : lam_g[e];
+      const float ps = warm_i ? psi_g[e] : 0.f;
+      const float lm = warm_i ? lam_g[e] : 0.f;
       psi_p[e] = ps;
       lam_p[e] = lm;
     }
@@ -1303,6 +1306,11 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(Params P) {
     if (P.fixed_iters <= 0 && total == 0u) { ++iter; break; }
   }
   if (b == 0 && tid == 0) P.err[4] = iter;
+  // every CTA is past its prologue (the grid barriers): record which
+  // instances met Conv, the next DLMPC_WARM_CONVERGED step reads it (each
+  // thread of CTA 0 reads the counts it wrote itself)
+  if (b == 0)
+    for (int e = tid; e < P.n_inst; e += blockDim.x) P.conv_prev[e] = (ok && P.inst_iters[e] > 0) ? 1 : 0;
 
   // ---- epilogue: final Psi/Lambda (from the compact iterate, or the resident
   // state written back), dynamics

@@ -157,3 +157,57 @@ def heldout_states(problem, seed: int, trajectories: int, steps: int):
         x, xn = xn, x
     s.close()
     return np.array(states), np.array(status)
+
+
+def heldout_trajectories(problem, seed: int, trajectories: int, steps: int):
+    """Closed loops from held-out x(0) draws (previous-step warm starts, one
+    batched context): the visited states [trajectories, steps, n_sub, nx]
+    and the status of each step [trajectories, steps]."""
+    states, status = heldout_states(problem, seed, trajectories, steps)
+    n, nx = problem.n_sub, problem.nx
+    # heldout_states lists the states step-major: step tau, then trajectory b
+    st = states.reshape(steps, trajectories, n, nx).transpose(1, 0, 2, 3)
+    ss = status.reshape(steps, trajectories).T
+    return st, ss
+
+
+def evaluate_starts(problem, mlp, trajectories, status, plant: bool = True):
+    """Every visited state of every held-out trajectory solved on one
+    single-instance context, in trajectory order, three ways to the same
+    eps: cold (zeros), learned (the network's start), previous (the solution
+    of the trajectory's previous state, the way a running controller starts).
+    Only steps whose cold solve converged are kept.  Returns per-start arrays
+    of iterations, statuses and whole-step milliseconds (CUDA events)."""
+    import torch
+    import paper_2103_14990_gb300 as pkg
+    s = pkg.Solver([problem])
+    s.set_option(pkg.OPT_LEARN_PLANT, 1 if plant else 0)
+    s.set_option(pkg.OPT_TIMING, 1)
+    s.attach_mlp(mlp)
+    u = torch.empty(problem.n_sub, problem.nu, device="cuda")
+    out = {k: {"iters": [], "status": [], "ms": []} for k in ("cold", "learned", "previous")}
+    for tr, stt in zip(trajectories, status):
+        xs = [torch.tensor(x.astype(np.float32), device="cuda") for x in tr]
+        keep = []
+        for k, x in enumerate(xs):
+            _, st = s.step(x, u, None, warm=pkg.WARM_COLD)
+            if st[0]["status"] == pkg.DLMPC_OK and stt[k] == pkg.DLMPC_OK:
+                keep.append(k)
+                out["cold"]["iters"].append(st[0]["iters"])
+                out["cold"]["status"].append(st[0]["status"])
+                out["cold"]["ms"].append(s.timing()[1])
+        for k in keep:
+            _, st = s.step(xs[k], u, None, warm=pkg.WARM_LEARNED)
+            out["learned"]["iters"].append(st[0]["iters"])
+            out["learned"]["status"].append(st[0]["status"])
+            out["learned"]["ms"].append(s.timing()[1])
+        # the previous-step start: walk the trajectory in order, each step
+        # warm-started from the one before (all steps run, kept ones counted)
+        for k, x in enumerate(xs):
+            _, st = s.step(x, u, None, warm=pkg.WARM_COLD if k == 0 else pkg.WARM_PREVIOUS)
+            if k in keep:
+                out["previous"]["iters"].append(st[0]["iters"])
+                out["previous"]["status"].append(st[0]["status"])
+                out["previous"]["ms"].append(s.timing()[1])
+    s.close()
+    return {k: {f: np.array(v) for f, v in d.items()} for k, d in out.items()}

@@ -47,7 +47,7 @@ def max_patch_rel(lay, got, ref, floor=1e-7, floor_vals=None, offset=0):
 
 
 def stopped_closed_loop(p, torch, warm_name, steps, iter_tol=0.02, check_next=False, tune_iters=None,
-                        oracle=None):
+                        oracle=None, max_iter=None):
     """Stopped-run parity (Conv on) of a closed loop, both sides solving from
     the oracle's x(tau) at every MPC step.  Per step:
       1. the GPU stops on its own Conv: status converged and an iteration
@@ -63,21 +63,24 @@ def stopped_closed_loop(p, torch, warm_name, steps, iter_tol=0.02, check_next=Fa
     the comparison at 1e-4 is made at a matched count.  Returns a summary."""
     import paper_2103_14990_gb300 as pkg
     o = oracle if oracle is not None else O.Oracle(p)
-    xs, us, its, stats = o.run_mpc(steps, warm=warm_name)
+    xs, us, its, stats = o.run_mpc(steps, warm=warm_name, max_iter=max_iter)
     s = pkg.Solver([p])
+    if max_iter is not None:
+        s.set_option(pkg.OPT_MAX_ITER, max_iter)
     if tune_iters is not None:
         s.autotune(torch.tensor(p.x0.astype(np.float32), device="cuda"), iters=tune_iters)
     saved = None
     out = {"matched_counts": 0, "iters_gpu": [], "iters_oracle": list(its), "worst_u": 0.0, "worst_psi_patch": 0.0}
     for tau in range(steps):
         x = torch.tensor(xs[tau].astype(np.float32), device="cuda")
-        warm = pkg.WARM_PREVIOUS if (warm_name == "previous" and tau > 0) else pkg.WARM_COLD
+        warm = pkg.WARM_PREVIOUS if (tau > 0 and (warm_name == "previous" or (
+            warm_name == "converged" and stats[tau - 1].status == O.STATUS_CONVERGED))) else pkg.WARM_COLD
         u = torch.zeros(p.n_sub, p.nu, device="cuda")
         xn = torch.zeros(p.n_sub, p.nx, device="cuda")
         if warm == pkg.WARM_PREVIOUS:
             s.set_state(*saved)
         rc, st = s.step(x, u, xn, warm=warm)
-        assert st[0]["status"] == 0, (tau, st)
+        assert st[0]["status"] == stats[tau].status, (tau, st)
         assert abs(st[0]["iters"] - its[tau]) <= max(3, iter_tol * its[tau]), (tau, st[0]["iters"], its[tau])
         out["iters_gpu"].append(st[0]["iters"])
         ug = u.cpu().numpy()

@@ -751,3 +751,40 @@ def test_contexts_with_different_plans_interleave(torch):
     run_fixed(s2, torch, small.x0, 5, export=False)
     s1.close()
     s2.close()
+
+
+def test_warm_start_from_converged_steps_only(torch):
+    """DLMPC_WARM_CONVERGED decides per instance on the device: a closed loop
+    run with it gives the bits of the same loop whose host picks, step by
+    step, the previous state after a converged step and zeros after a step
+    stopped at max_iter; and the loop matches the oracle's "converged"
+    policy (stopped-run parity at 1e-4, capped steps included)."""
+    import paper_2103_14990_gb300 as pkg
+    p = I.chain10()
+    cap = 252                                     # steps 0-2 stop at the cap, the others converge
+    o = O.Oracle(p)
+    _, _, its, stats = o.run_mpc(p.mpc_steps, warm="converged", max_iter=cap)
+    assert 0 < sum(s.status == O.STATUS_CONVERGED for s in stats) < p.mpc_steps
+    runs = []
+    for mode in ("device", "host"):
+        s = gpu_solver([p], torch)
+        s.set_option(pkg.OPT_MAX_ITER, cap)
+        x = torch.tensor(p.x0.astype(np.float32), device="cuda")
+        xn = torch.zeros_like(x)
+        u = torch.zeros(p.n_sub, 1, device="cuda")
+        rec, last = [], None
+        for tau in range(p.mpc_steps):
+            if mode == "device":
+                warm = pkg.WARM_CONVERGED
+            else:
+                warm = pkg.WARM_PREVIOUS if (last is not None and last == 0) else pkg.WARM_COLD
+            rc, st = s.step(x, u, xn, warm=warm)
+            last = st[0]["status"]
+            rec.append((st[0]["iters"], last, u.cpu().numpy().copy()))
+            x, xn = xn, x
+        runs.append(rec)
+        s.close()
+    for a, b in zip(*runs):
+        assert a[0] == b[0] and a[1] == b[1] and np.array_equal(a[2], b[2])
+    out = stopped_closed_loop(p, torch, "converged", p.mpc_steps, max_iter=cap)
+    assert out["iters_oracle"] == list(its)

@@ -973,3 +973,19 @@ def test_planted_conv_mistake_is_caught(monkeypatch, kind):
     _plant_conv(monkeypatch, kind)
     with pytest.raises(AssertionError):
         test_conv_first_iteration_closed_form()
+
+
+def test_converged_warm_policy_reduces_to_its_two_limits():
+    """The "converged" warm start is the previous-step start when every step
+    meets Conv and the cold start when every step stops at max_iter."""
+    p = I.make_instance(6, 4, 1, seed=4, boxes=False, x0_dist="normal", mpc_steps=4)
+    o = O.Oracle(p)
+    a = o.run_mpc(4, warm="converged")
+    b = o.run_mpc(4, warm="previous")
+    assert all(s.status == O.STATUS_CONVERGED for s in a[3])
+    assert a[2] == b[2] and np.array_equal(a[1], b[1])
+    c = o.run_mpc(4, warm="converged", max_iter=3)
+    d = o.run_mpc(4, warm="cold", max_iter=3)
+    e = o.run_mpc(4, warm="previous", max_iter=3)
+    assert all(s.status == O.STATUS_MAX_ITER for s in c[3])
+    assert np.array_equal(c[1], d[1]) and not np.array_equal(c[1], e[1])
