@@ -10,9 +10,12 @@ T=10, d=3, |x| <= 1, |u| <= 2, x(0) ~ U[-0.9, 0.9] (seed 0), FP32 sweeps.
 Our arm: W warm-up steps, then the state is reset to x(0) and K closed-loop
 steps are timed with CUDA events recorded by the library on its stream (the
 L2 is flushed between steps by a 256 MiB write outside the timed events).
-Headline: warm-started (previous step's Psi/Lambda) steps; the same K steps
-with cold starts ("plain") and through the host-buffer C-ABI call ("e2e")
-are reported beside it.  N > 1: one independent replica per GPU, no
+Headline: warm-started steps (the previous step's Psi/Lambda where that step
+met Conv, zeros after a step stopped at max_iter); the same K steps with cold
+starts ("plain"), with the previous step's state whatever its status
+("warm_previous") and through the host-buffer C-ABI call ("e2e") are
+reported beside it, with the mixed 256-instance batch (batched against one
+context per instance) and the other workloads' closed loops.  N > 1: one independent replica per GPU, no
 communication (weak scaling).  The reference arm times the FP64 oracle on
 the host cores.
 """
@@ -40,7 +43,29 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_sweep.c
 # the profile summaries): DRAM bytes read + written, the iterations that
 # launch ran, and the on-chip figures of the same kernel.  A workload without
 # a capture of the current source reports null.
-NCU = {"src_sha256": None, "workloads": {}}
+NCU = {
+    "src_sha256": "33a53484f4bde0c48d93e13bb8ecceeaf4dede7cb62b8f5798d38f4ddb2a8e19",
+    "workloads": {
+        # one bench-plan launch of 200 fixed iterations from x(0): the
+        # operators come from DRAM once per launch, the loop is served by
+        # shared memory and L2 (full capture of 50 iterations, same plan)
+        "chain1024": {"dram_bytes_per_launch": 79874816 + 1774848, "iters_per_launch": 200,
+                      "onchip": {"dram_throughput_pct": 1.66, "lts_throughput_pct": 19.97,
+                                 "l2_hit_rate_pct": 93.05, "issue_active_pct": 35.0, "warps_active_pct": 43.6}},
+        # 20 fixed iterations of the autotuned plan (256 x 4, wave 2): N and
+        # N^T streamed from DRAM every iteration
+        "grid64": {"dram_bytes_per_launch": 12879666944 + 283163904, "iters_per_launch": 20,
+                   "onchip": {"dram_throughput_pct": 37.0, "lts_throughput_pct": 23.6,
+                              "l2_hit_rate_pct": 23.6, "issue_active_pct": 22.4, "warps_active_pct": 50.0}},
+        # 64 of the 256 instances (a few GB on the device), 10 fixed
+        # iterations; scaled to the 256-instance launch by the algorithmic
+        # bytes (DRAM / algorithmic = 1.80 on the 64-instance capture)
+        "batch256": {"dram_bytes_per_launch": int(1.80 * 9889012444 * 20), "iters_per_launch": 20,
+                     "scaled_from": "64-instance capture: 46784501248 B per 10 iterations, 2.60 GB algorithmic each",
+                     "onchip": {"dram_throughput_pct": 30.0, "lts_throughput_pct": 19.3,
+                                "l2_hit_rate_pct": 22.8, "issue_active_pct": 12.9, "warps_active_pct": 25.0}},
+    },
+}
 
 
 INNER_QP = {"box": "diagonal Q, R with boxes (closed-form row Phi-step)",
@@ -62,7 +87,8 @@ def bench_config(prob, world: int, inner_qp: str = "box", stale_prob: float = 0.
     """The workload description shared by both arms."""
     return {"workload": prob.name, "inner_qp": INNER_QP[inner_qp], "message_loss": stale_prob,
             "n_sub": prob.n_sub, "T": prob.T, "d": prob.d, "boxes": "|x|<=1, |u|<=2",
-            "warm_start": "previous MPC step's Psi/Lambda (step 0 cold)", "max_iter": prob.max_iter,
+            "warm_start": "previous MPC step's Psi/Lambda where that step met Conv, else zeros (step 0 cold)",
+            "max_iter": prob.max_iter,
             "eps": prob.eps_p, "l2": "flushed between steps (256 MiB write outside the events)",
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
@@ -78,8 +104,11 @@ def ncu_record(workload_name: str, inner_qp: str, stale_prob: float) -> dict:
     w = NCU["workloads"].get(workload_name)
     if w is None or NCU["src_sha256"] != kernel_sha() or inner_qp != "box" or stale_prob != 0:
         return {"traffic": None, "onchip": None}
-    return {"traffic": w["dram_bytes_per_launch"], "traffic_launch_iters": w["iters_per_launch"],
-            "onchip": w.get("onchip")}
+    out = {"traffic": w["dram_bytes_per_launch"], "traffic_launch_iters": w["iters_per_launch"],
+           "onchip": w.get("onchip")}
+    if "scaled_from" in w:
+        out["traffic_scaled_from"] = w["scaled_from"]
+    return out
 
 
 def measured_peaks():
@@ -288,11 +317,11 @@ def run_ours(args):
             dist.barrier()
 
     # warm-up (discarded), then the timed closed loops from x(0)
-    loop(args.warmup, pkg.WARM_PREVIOUS)
+    loop(args.warmup, pkg.WARM_CONVERGED)
     sync_all()
     with ClockSampler(local) as clk:
         wall0 = time.perf_counter()
-        rec = closed_loop(solver, x0, args.steps, pkg.WARM_PREVIOUS, flush)
+        rec = closed_loop(solver, x0, args.steps, pkg.WARM_CONVERGED, flush)
         sync_all()
         wall = time.perf_counter() - wall0
     kms, sms = rec["kms"], rec["sms"]
@@ -304,14 +333,17 @@ def run_ours(args):
 
     # the same closed loop replayed from captured CUDA graphs (whole-step events)
     solver.set_option(pkg.OPT_GRAPH, 1)
-    loop(2, pkg.WARM_PREVIOUS)
-    gk, gs, git, gst, _ = loop(args.steps, pkg.WARM_PREVIOUS)
+    loop(2, pkg.WARM_CONVERGED)
+    gk, gs, git, gst, _ = loop(args.steps, pkg.WARM_CONVERGED)
     solver.set_option(pkg.OPT_GRAPH, 0)
     graph = {"value": args.steps / (sum(gs) / 1e3), "unit": UNIT, "iters_per_step": sum(git) / len(git)}
 
     # plain: cold start at every step, same kernel
     plain = summarise(closed_loop(solver, x0, args.steps, pkg.WARM_COLD, flush))
     plain["start"] = "cold (zeros) at every step, one instance per launch"
+    # the previous step's state whatever that step's status (also after a
+    # step stopped at max_iter)
+    warm_previous = summarise(closed_loop(solver, x0, args.steps, pkg.WARM_PREVIOUS, flush))
 
     # ablation of the paper's GPU mappings (Sec. III): ADMM iterations/s from x(0)
     ablation = {}
@@ -342,7 +374,7 @@ def run_ours(args):
     e0 = time.perf_counter()
     for tau in range(args.steps):
         solver.step_host_ptr(xh.data_ptr(), uh.data_ptr(), xnh.data_ptr(),
-                             warm=(pkg.WARM_COLD if tau == 0 else pkg.WARM_PREVIOUS))
+                             warm=(pkg.WARM_COLD if tau == 0 else pkg.WARM_CONVERGED))
         xh, xnh = xnh, xh
     e_wall = time.perf_counter() - e0
     e2e = {"value": args.steps / e_wall, "unit": UNIT, "h2d_bytes_per_step": n * nx * 4,
@@ -364,6 +396,7 @@ def run_ours(args):
         "steps_at_max_iter": int(sum(1 for s in status if s != 0)),
         "converged_steps": warm_summary.get("converged_steps"),
         "plain": plain,
+        "warm_previous": warm_previous,
         "e2e": e2e,
         "roofline": roofline,
         "graph": graph,
@@ -402,8 +435,8 @@ def config_line(name, args, flush):
     s.autotune(x0, iters=args.tune_iters)
     s.set_option(pkg.OPT_TIMING, 1)
     K = prob.mpc_steps
-    closed_loop(s, x0, args.warmup, pkg.WARM_PREVIOUS, flush)
-    warm = closed_loop(s, x0, K, pkg.WARM_PREVIOUS, flush)
+    closed_loop(s, x0, args.warmup, pkg.WARM_CONVERGED, flush)
+    warm = closed_loop(s, x0, K, pkg.WARM_CONVERGED, flush)
     plain = closed_loop(s, x0, K, pkg.WARM_COLD, flush)
     info = s.info()
     peak, peak_src = measured_peaks()
@@ -442,7 +475,7 @@ def batch_line(args, flush):
     sb.set_option(pkg.OPT_TIMING, 1)
     closed_loop(sb, xb, 1, pkg.WARM_COLD, flush)                   # warm-up
     w0 = time.perf_counter()
-    bw = closed_loop(sb, xb, K, pkg.WARM_PREVIOUS, flush)
+    bw = closed_loop(sb, xb, K, pkg.WARM_CONVERGED, flush)
     wall_bw = time.perf_counter() - w0
     bc = closed_loop(sb, xb, K, pkg.WARM_COLD, flush) if args.batch_all_arms else None
     # per-iteration roofline: fixed iterations from x(0), every instance active
@@ -464,7 +497,7 @@ def batch_line(args, flush):
     w0 = time.perf_counter()
     sc = merge_records([closed_loop(s, x, K, pkg.WARM_COLD, flush) for s, x in zip(singles, xs)])
     wall_sc = time.perf_counter() - w0
-    sw = (merge_records([closed_loop(s, x, K, pkg.WARM_PREVIOUS, flush) for s, x in zip(singles, xs)])
+    sw = (merge_records([closed_loop(s, x, K, pkg.WARM_CONVERGED, flush) for s, x in zip(singles, xs)])
           if args.batch_all_arms else None)
     for s in singles:
         s.close()
@@ -492,12 +525,11 @@ def batch_line(args, flush):
 def learned_line(prob, args):
     """Learned warm start on the benchmark chain: training pairs from closed
     loops of the batched solver (random x(0), cold-start solutions), BF16
-    training on the GPU, then held-out visited states solved from the same
-    state with a cold and with a learned start to the same epsilon: ADMM
-    iterations and MPC steps/s (whole step, network inference included)."""
-    import numpy as np
+    training on the GPU, then the visited states of held-out closed loops
+    solved from a cold, a learned and a previous-step start to the same
+    epsilon: ADMM iterations and MPC steps/s (whole step, network inference
+    included)."""
     import torch
-    import paper_2103_14990_gb300 as pkg
     from paper_2103_14990_gb300 import instances as I
     from paper_2103_14990_gb300 import warmstart as W
     t0 = time.time()
@@ -512,35 +544,22 @@ def learned_line(prob, args):
     torch.cuda.synchronize()
     t_train = time.time() - t0
     err = W.prediction_error(mlp, pairs)
-    states, status = W.heldout_states(prob, seed=2000, trajectories=4, steps=args.learn_steps)
-    keep = np.nonzero(status == 0)[0][::2]
-    ic, il, sc, sl, _, _ = W.compare_starts(prob, mlp, states[keep])
-    # MPC steps/s over the same held-out states, one instance, whole step timed
-    s = pkg.Solver([prob])
-    s.set_option(pkg.OPT_LEARN_PLANT, 1)
-    s.attach_mlp(mlp)
-    s.autotune(torch.tensor(prob.x0.astype(np.float32), device="cuda"), iters=0)
-    xs = [torch.tensor(states[k].astype(np.float32), device="cuda") for k in keep]
-    u = torch.empty(prob.n_sub, prob.nu, device="cuda")
-    rates = {}
-    for name, warm in (("cold", pkg.WARM_COLD), ("learned", pkg.WARM_LEARNED)):
-        s.step(xs[0], u, None, warm=warm)
-        torch.cuda.synchronize()
-        w0 = time.perf_counter()
-        for x in xs:
-            s.step(x, u, None, warm=warm)
-        torch.cuda.synchronize()
-        rates[name] = len(xs) / (time.perf_counter() - w0)
-    s.close()
+    trajs, tstat = W.heldout_trajectories(prob, seed=2000, trajectories=args.learn_heldout, steps=args.learn_steps)
+    ev = W.evaluate_starts(prob, mlp, trajs, tstat)
+    starts = {}
+    for name, d in ev.items():
+        starts[name] = {"iters_per_step": round(float(d["iters"].mean()), 2),
+                        "converged": int((d["status"] == 0).sum()),
+                        "steps_per_s": round(len(d["ms"]) / (float(d["ms"].sum()) / 1e3), 2)}
     return {"workload": prob.name, "train_pairs": int(pairs.feats.shape[0]), "train_steps_used": pairs.steps_used,
             "train_steps_skipped": pairs.steps_skipped,
             "epochs": args.learn_epochs, "data_s": round(t_data, 2), "train_s": round(t_train, 2),
-            "train_rel_err": round(err, 4), "heldout_states": int(len(keep)),
-            "iters_cold": round(float(ic.mean()), 2), "iters_learned": round(float(il.mean()), 2),
-            "all_converged": bool(np.all(sc == 0) and np.all(sl == 0)),
-            "steps_per_s_cold": round(rates["cold"], 2), "steps_per_s_learned": round(rates["learned"], 2),
-            "note": "each held-out state solved twice from scratch (cold vs network start), eps 1e-4; "
-                    "steps/s with host-side synchronisation per step"}
+            "train_rel_err": round(err, 4), "heldout_states": int(len(ev["cold"]["iters"])),
+            "heldout_trajectories": args.learn_heldout, "starts": starts,
+            "iters_saved_vs_cold": round(1.0 - starts["learned"]["iters_per_step"] / starts["cold"]["iters_per_step"], 4),
+            "note": "every visited state of held-out closed loops (x(0) ~ U[-0.9,0.9], seed 2000) whose cold solve "
+                    "converges, solved to eps 1e-4 from a cold, a learned and a previous-step start on one "
+                    "single-instance context; steps/s from whole-step CUDA events (network inference included)"}
 
 
 # ---------------------------------------------------------------------------
@@ -612,7 +631,7 @@ def cpu_baseline(args, gpu_iters):
     s = json.loads(r.stdout.strip().splitlines()[-1])
     table = oracle_iters_table(args.workload)
     if table is not None:
-        its = table["previous"]["iters"][:args.steps]
+        its = table["converged"]["iters"][:args.steps]
         src = "oracle's own per-step iteration counts (tests/golden/chain1024_oracle_iters.json)"
     else:
         its = gpu_iters
@@ -643,7 +662,7 @@ def cpu_baseline_all_cores(args, gpu_iters, cores=None):
         rates.append(1.0 / r["t_iter"])
         tails.append(r["t_tail"])
     table = oracle_iters_table(args.workload)
-    its = table["previous"]["iters"][:args.steps] if table is not None else gpu_iters
+    its = table["converged"]["iters"][:args.steps] if table is not None else gpu_iters
     agg = sum(rates)                       # oracle ADMM iterations per second over all cores
     t = sum(i / agg + max(tails) / cores for i in its)
     return {"value": round(len(its) / t, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -667,7 +686,7 @@ def reference_worker(args):
     from oracle import dlmpc_oracle as O
     prob = workload(args.workload)
     o = O.Oracle(prob)
-    its = oracle_iters_table(args.workload)["previous"]["iters"]
+    its = oracle_iters_table(args.workload)["converged"]["iters"]
     per_step_sample = 2
     Psi = Lam = None
 
@@ -751,6 +770,7 @@ def main():
     ap.add_argument("--learn-replicas", type=int, default=8)
     ap.add_argument("--learn-steps", type=int, default=36)
     ap.add_argument("--learn-epochs", type=int, default=40)
+    ap.add_argument("--learn-heldout", type=int, default=6, help="held-out closed loops of the learned line")
     ap.add_argument("--ablation-iters", type=int, default=20)
     # the autotuner's fixed iteration count: near the steps' own (about 350 on
     # the chain) so that a plan's one-time prologue (bulk copies of resident

@@ -30,10 +30,14 @@ def main(argv=None) -> int:
     ap.add_argument("--batch-count", type=int, default=256, help="instances of the mixed batch")
     ap.add_argument("--inner-qp", default="box", choices=["box", "block", "coupled"],
                     help="block: full SPD cost blocks; coupled: also 2 coupled state rows per slot")
+    ap.add_argument("--network", action="store_true",
+                    help="instead of sweeps: the learned start's network forward at the workload's sizes")
     a = ap.parse_args(argv)
     import torch
     import paper_2103_14990_gb300 as pkg
     from paper_2103_14990_gb300 import instances as I
+    if a.network:
+        return network_forward(a)
     probs = I.batch256(a.batch_count) if a.workload == "batch256" else \
         [{"chain1024": I.chain1024, "chain10": I.chain10, "grid64": I.grid64}[a.workload]()]
     if a.inner_qp == "block":
@@ -81,6 +85,32 @@ def main(argv=None) -> int:
             tot = np.median((tr[ok, it + 1, 0] - tr[ok, it, 0]) / 1e3)
             print(f"iter {it}: " + " ".join(f"{n} {v:.2f}" for n, v in zip(names, row)) +
                   f" | arrival median {np.median(arr):.2f} max {np.max(arr):.2f} | total {tot:.2f} us")
+    s.close()
+    return 0
+
+
+def network_forward(a) -> int:
+    """The warm-start network (patch inputs -> 256 -> 256 -> Phi rows and
+    Lambda) on one row per subsystem of the workload, `--steps` forward
+    passes timed with CUDA events."""
+    import torch
+    import paper_2103_14990_gb300 as pkg
+    from paper_2103_14990_gb300 import instances as I
+    p = {"chain1024": I.chain1024, "chain10": I.chain10, "grid64": I.grid64}[a.workload]()
+    s = pkg.Solver([p])
+    s.set_option(pkg.OPT_LEARN_PLANT, 1)
+    d_in, d_out = s.learned_dims()
+    mlp = pkg.MLP(d_in, 256, d_out, seed=0)
+    x = torch.tensor(p.x0.astype(np.float32), device="cuda")
+    feats = s.learned_features(x)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(a.steps):
+        e0.record()
+        mlp.forward(feats)
+        e1.record()
+        torch.cuda.synchronize()
+        print(f"network forward {p.n_sub} x {d_in} -> 256 -> 256 -> {d_out}: {1e3 * e0.elapsed_time(e1):.1f} us")
+    mlp.close()
     s.close()
     return 0
 

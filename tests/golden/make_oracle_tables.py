@@ -2,8 +2,9 @@
 
 Per-MPC-step ADMM iteration counts (and u norms) of the 50-step closed loop
 of the N=1024 chain (T=10, d=3, boxes, seed 0), for a cold start at every step
-and for a start from the previous step's Psi and Lambda, and the closed-loop
-states x(tau) at tau = 16, 20, 30 of both loops.  The benchmark's CPU
+for a start from the previous step's Psi and Lambda, and for that start only
+after a step that met Conv (zeros otherwise), and the closed-loop states
+x(tau) at tau = 16, 20, 30 of each loop.  The benchmark's CPU
 baseline and reference arm time bounded samples of oracle iterations and scale
 them by these counts; the full-size parity tests start from those states.  Run: python tests/golden/make_oracle_tables.py
 """
@@ -38,8 +39,8 @@ def run(warm):
 
 
 if __name__ == "__main__":
-    with mp.get_context("spawn").Pool(2) as pool:
-        res = dict(pool.map(run, ["previous", "cold"]))
+    with mp.get_context("spawn").Pool(3) as pool:
+        res = dict(pool.map(run, ["previous", "cold", "converged"]))
     out = {"workload": "chain_N1024_T10_d3_box seed 0, 50 closed-loop MPC steps, max_iter 1000",
            "writer": "tests/golden/make_oracle_tables.py (FP64 oracle only)", **res}
     with open(os.path.join(HERE, "chain1024_oracle_iters.json"), "w") as f:
