@@ -188,3 +188,20 @@ def test_struct_layout_matches_header(tmp_path):
     for f, off in zip(fields, vals[1:1 + len(fields)]):
         assert getattr(pkg.Problem_C, f).offset == off, f
     assert vals[-1] == ctypes.sizeof(pkg.Stats_C)
+
+
+def test_update_plant_needs_a_precomputed_context(clib):
+    """The plant update replaces operators: before dlmpc_precompute there are
+    none, and the call is refused without touching the device."""
+    p = I.make_instance(8, 4, 1, seed=4, boxes=True)
+    rc, ctx, _ = _setup(clib, [p])
+    assert rc == 0
+    sub = np.array([3], np.int32)
+    ad = np.ascontiguousarray(p.A_diag[3:4])
+    ao = np.ascontiguousarray(p.A_off[p.adj_ptr[3]:p.adj_ptr[4]])
+    bb = np.ascontiguousarray(p.B[3:4])
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = clib.dlmpc_update_plant(ctx, 1, sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 ad.ctypes.data_as(dp), ao.ctypes.data_as(dp), bb.ctypes.data_as(dp))
+    assert rc == pkg.DLMPC_ERR_ARG and b"precompute" in clib.dlmpc_last_error(ctx)
+    clib.dlmpc_destroy(ctx)
