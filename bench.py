@@ -44,26 +44,26 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_sweep.c
 # launch ran, and the on-chip figures of the same kernel.  A workload without
 # a capture of the current source reports null.
 NCU = {
-    "src_sha256": "33a53484f4bde0c48d93e13bb8ecceeaf4dede7cb62b8f5798d38f4ddb2a8e19",
+    "src_sha256": "63f3813406c2a166824893c604c3a10e93c70f77e9770f59382758e22aa1908c",
     "workloads": {
         # one bench-plan launch of 200 fixed iterations from x(0): the
         # operators come from DRAM once per launch, the loop is served by
         # shared memory and L2 (full capture of 50 iterations, same plan)
-        "chain1024": {"dram_bytes_per_launch": 79874816 + 1774848, "iters_per_launch": 200,
-                      "onchip": {"dram_throughput_pct": 1.66, "lts_throughput_pct": 19.97,
-                                 "l2_hit_rate_pct": 93.05, "issue_active_pct": 35.0, "warps_active_pct": 43.6}},
+        "chain1024": {"dram_bytes_per_launch": 83254528 + 2711552, "iters_per_launch": 200,
+                      "onchip": {"dram_throughput_pct": 1.58, "lts_throughput_pct": 21.70,
+                                 "l2_hit_rate_pct": 93.64, "issue_active_pct": 38.2, "warps_active_pct": 43.9}},
         # 20 fixed iterations of the autotuned plan (256 x 4, wave 2): N and
         # N^T streamed from DRAM every iteration
-        "grid64": {"dram_bytes_per_launch": 12879666944 + 283163904, "iters_per_launch": 20,
-                   "onchip": {"dram_throughput_pct": 37.0, "lts_throughput_pct": 23.6,
-                              "l2_hit_rate_pct": 23.6, "issue_active_pct": 22.4, "warps_active_pct": 50.0}},
+        "grid64": {"dram_bytes_per_launch": 12880553472 + 282576128, "iters_per_launch": 20,
+                   "onchip": {"dram_throughput_pct": 37.3, "lts_throughput_pct": 23.8,
+                              "l2_hit_rate_pct": 23.8, "issue_active_pct": 22.7, "warps_active_pct": 49.9}},
         # 64 of the 256 instances (a few GB on the device), 10 fixed
         # iterations; scaled to the 256-instance launch by the algorithmic
         # bytes (DRAM / algorithmic = 1.80 on the 64-instance capture)
         "batch256": {"dram_bytes_per_launch": int(1.80 * 9889012444 * 20), "iters_per_launch": 20,
-                     "scaled_from": "64-instance capture: 46784501248 B per 10 iterations, 2.60 GB algorithmic each",
-                     "onchip": {"dram_throughput_pct": 30.0, "lts_throughput_pct": 19.3,
-                                "l2_hit_rate_pct": 22.8, "issue_active_pct": 12.9, "warps_active_pct": 25.0}},
+                     "scaled_from": "64-instance capture: 46783720448 B per 10 iterations, 2.60 GB algorithmic each",
+                     "onchip": {"dram_throughput_pct": 30.7, "lts_throughput_pct": 19.7,
+                                "l2_hit_rate_pct": 23.0, "issue_active_pct": 13.4, "warps_active_pct": 25.0}},
     },
 }
 
@@ -248,6 +248,9 @@ def summarise(rec, unit=UNIT):
            "steps_at_max_iter": int((stt != 0).sum())}
     if n_inst > 1:
         out["launch_iters_per_step"] = round(float(it.max(axis=1).mean()), 2)
+        # per MPC step: whole-step ms, mean iterations, instances at the cap
+        out["by_step"] = [[round(rec["sms"][t], 3), round(float(it[t].mean()), 1), int((stt[t] != 0).sum())]
+                          for t in range(K)]
     else:
         conv = [t for t in range(K) if rec["status"][t][0] == 0]
         if conv:
