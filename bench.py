@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MPC steps/s & ADMM iters/s, batched+warm-start vs plain at 1e-4 rel; HBM GB/s"
 UNIT = "MPC steps/s"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_sweep.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_sweep.cuh")
 # Counters of one sweep_kernel launch per workload from ncu captures of the
 # kernel source whose sha256 is given (the capture commands are recorded with
 # the profile summaries): DRAM bytes read + written, the iterations that

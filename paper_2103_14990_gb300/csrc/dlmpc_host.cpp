@@ -26,7 +26,7 @@ namespace dlmpc {
 cudaError_t launch_factor(const FactorParams &p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_repack(const Item *scratch_items, const Item *items, int n_items, const float *src, float *dst,
                           cudaStream_t s);
-const void *sweep_kernel_ptr(int nx, int gt, bool blk);
+const void *sweep_kernel_ptr(int nx, int gt, bool blk, int threads);
 int sweep_group_floats(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad, int max_kpad, int max_nmem);
 cudaStream_t mlp_stream(const dlmpc_mlp *mlp);
 cudaError_t launch_sweep(const Params &P, int gt, int grid, size_t smem, cudaStream_t s);
@@ -828,19 +828,20 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
   CK(cudaGetDevice(&dev), "cudaGetDevice");
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
   CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-  const void *fn = sweep_kernel_ptr(nx, gt, false);
-  if (!fn) return ctx->fail(DLMPC_ERR_ARG, "no sweep kernel for this nx / group size");
-  const void *fn_blk = sweep_kernel_ptr(nx, gt, true);  // full cost blocks (64 and 128 threads)
-  if (ctx->block_cost && !fn_blk)
-    return ctx->fail(DLMPC_ERR_ARG, "full cost blocks need 64 or 128 threads per group");
-  cudaFuncAttributes fa{};
-  CK(cudaFuncGetAttributes(&fa, fn), "cudaFuncGetAttributes");
-  const int64_t budget = ((int64_t)smem_optin - (int64_t)fa.sharedSizeBytes - 64) / 4;  // floats
   const int n = ctx->n_sub;
   // default: every SM busy, groups per CTA trimmed to the items per CTA;
   // an explicit shape keeps its group count and trims the grid instead
   const int grid = exact_groups ? std::max(1, std::min(sms, (n + ng - 1) / ng)) : std::max(1, std::min(sms, n));
   if (!exact_groups) ng = std::max(1, std::min(ng, (n + grid - 1) / grid));
+  // the kernel of the final CTA size (its register tier)
+  const void *fn = sweep_kernel_ptr(nx, gt, false, gt * ng);
+  if (!fn) return ctx->fail(DLMPC_ERR_ARG, "no sweep kernel for this nx / group size");
+  const void *fn_blk = sweep_kernel_ptr(nx, gt, true, gt * ng);  // full cost blocks (64 and 128 threads)
+  if (ctx->block_cost && !fn_blk)
+    return ctx->fail(DLMPC_ERR_ARG, "full cost blocks need 64 or 128 threads per group");
+  cudaFuncAttributes fa{};
+  CK(cudaFuncGetAttributes(&fa, fn), "cudaFuncGetAttributes");
+  const int64_t budget = ((int64_t)smem_optin - (int64_t)fa.sharedSizeBytes - 64) / 4;  // floats
   std::vector<int32_t> all(n);
   std::iota(all.begin(), all.end(), 0);
   auto ctas = lpt(ctx, all, grid);
@@ -1518,7 +1519,7 @@ Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_d
 
 // Sets the sweep kernel's dynamic shared-memory limit to this context's plan.
 cudaError_t bind_sweep_smem(const dlmpc_ctx *ctx, bool blk) {
-  const void *fn = sweep_kernel_ptr(ctx->nx, ctx->gt, blk);
+  const void *fn = sweep_kernel_ptr(ctx->nx, ctx->gt, blk, ctx->gt * ctx->ng);
   if (!fn) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem);
 }
