@@ -474,7 +474,7 @@ def batch_line(args, flush):
     torch.cuda.synchronize()
     t_setup_b = time.time() - t0
     xb = torch.tensor(np.concatenate([p.x0 for p in probs]).astype(np.float32), device="cuda")
-    sb.autotune(xb, iters=10)
+    sb.autotune(xb, iters=20)
     sb.set_option(pkg.OPT_TIMING, 1)
     closed_loop(sb, xb, 1, pkg.WARM_COLD, flush)                   # warm-up
     w0 = time.perf_counter()

@@ -1744,7 +1744,7 @@ extern "C" int dlmpc_autotune(dlmpc_ctx *ctx, const float *x_dev, int32_t iters,
   std::vector<dlmpc_tune_entry> tried;
   dlmpc_tune_entry best{0, 0, 0, 0, std::numeric_limits<float>::infinity()};
   static const int kGt[] = {64, 96, 128, 256};
-  static const int kNg[] = {1, 2, 4, 6, 8, 12, 15};
+  static const int kNg[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 15};
   static const int kWave[] = {1, 2};
   static const int kRes[] = {2, 1};
   std::vector<std::tuple<int, int, int, int, int>> seen;

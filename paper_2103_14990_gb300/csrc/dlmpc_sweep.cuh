@@ -213,12 +213,14 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
   return z ^ (z >> 31);
 }
 
-// ... decides whether the row sums patch j sends to member m at the end of
-// iteration k are lost: draw n = (k N + j) N + m, lost when its top 53 bits
+// ... decides whether the row sums patch j sends to member m = *mp at the end
+// of iteration k are lost: draw n = (k N + j) N + m, lost when its top 53 bits
 // are below the threshold floor(p 2^53).  A lost message leaves the value the
-// receiver holds, so the writer copies the slot's current value forward.
-__device__ __forceinline__ float send(const Params &P, int iter, int j, int m, int idx, float fresh) {
+// receiver holds, so the writer copies the slot's current value forward.  The
+// member is read only when messages can be lost.
+__device__ __forceinline__ float send(const Params &P, int iter, int j, const int *mp, int idx, float fresh) {
   if (P.stale_thr == 0ull) return fresh;
+  const int m = *mp;
   const uint64_t N = (uint64_t)P.n_items;
   const uint64_t n = ((uint64_t)iter * N + (uint64_t)j) * N + (uint64_t)m;
   const float *Gcur = (iter & 1) ? P.G1 : P.G0;  // read this iteration, the receiver's value
@@ -868,9 +870,55 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
     }
     if (cp && r >= NX) cp[cpl + red] = rsum;
     const int gi = reinterpret_cast<const int *>(tab + mpos * MT)[3] + r;
-    Gnext[gi] = send(P, iter, it.sub, P.members[it.mem_off + mpos], gi, gsum);
+    Gnext[gi] = send(P, iter, it.sub, P.members + it.mem_off + mpos, gi, gsum);
   }
   finish_item<GT>(P, idx, it, extra, G, prim_f, dual_f, g, gt, lnc, iter);
+}
+
+// o = N y by rows of N (row-major, kpad floats per row, an odd number of
+// 16-byte units so the rows of a warp hit distinct bank groups) with the sums
+// of the flat pass over N^T, bit for bit: that pass gives partial q (q < QS)
+// the terms a = q (mod QS) in increasing a, fused multiply-adds from zero,
+// and the partials are added to zero in order q = 0, 1, ...; here partial q
+// takes the same terms in the same order (QS in {1, 2, 4} divides the four
+// entries of a 16-byte unit), and o[red] is that ordered sum.  The padded
+// entries of N and y are zeros and add exact zeros.  Used by the 80-register
+// tier only (ROWS): at 64 registers its live values would add spills to the
+// whole loop.
+__device__ __forceinline__ void rows_pass(const float *Nb, int dred, int kpad, const float *y, float *o_out, int QS,
+                                          int gt, int GT) {
+  for (int red = gt; red < dred; red += GT) {
+    const float *nr = Nb + red * kpad;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int c = 0; c < kpad; c += 4) {
+      const float4 n4 = *reinterpret_cast<const float4 *>(nr + c);
+      const float4 y4 = *reinterpret_cast<const float4 *>(y + c);
+      if (QS == 1) {
+        a0 = fmaf(n4.x, y4.x, a0);
+        a0 = fmaf(n4.y, y4.y, a0);
+        a0 = fmaf(n4.z, y4.z, a0);
+        a0 = fmaf(n4.w, y4.w, a0);
+      } else if (QS == 2) {
+        a0 = fmaf(n4.x, y4.x, a0);
+        a1 = fmaf(n4.y, y4.y, a1);
+        a0 = fmaf(n4.z, y4.z, a0);
+        a1 = fmaf(n4.w, y4.w, a1);
+      } else {
+        a0 = fmaf(n4.x, y4.x, a0);
+        a1 = fmaf(n4.y, y4.y, a1);
+        a2 = fmaf(n4.z, y4.z, a2);
+        a3 = fmaf(n4.w, y4.w, a3);
+      }
+    }
+    float o = 0.f;
+    o += a0;
+    if (QS >= 2) o += a1;
+    if (QS == 4) {
+      o += a2;
+      o += a3;
+    }
+    o_out[red] = o;
+  }
 }
 
 // Psi-comp, Lambda-comp and Conv of one patch on the compact iterate (every
@@ -893,7 +941,7 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
 // 16-byte column group g of every QS-th row starting at row q, so a warp reads
 // consecutive 16-byte units, and the QS partial sums per output are added
 // afterwards.
-template <int NX, int GT>
+template <int NX, int GT, bool ROWS>
 __device__ void project_compact(const Params &P, int idx, const Item &it, const float *tab, const float *rt,
                                 const float *extra, Group &G, const float *alpha, float *arena, float *Gnext, int g,
                                 int gt, unsigned *lnc, int iter, bool first, bool tr) {
@@ -935,16 +983,20 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
   group_sync(g, GT);
   if (tr) trace_point(P, iter, 7);
 
-  // pass 2: o = N y, flat over N^T (from L2 also for patches whose N is resident)
-  flat_pass<8>(NTb, k, dpad, G.t, G.part, gt, GT);
+  // pass 2: o = N y.  A patch whose N is resident takes it by rows from
+  // shared memory (no L2 traffic); the others read N^T from L2 flat.
+  const int nrg = dpad >> 2;
+  const int QS2 = GT >= nrg ? small_div(GT, nrg) : 1;
+  const bool by_rows = ROWS && it.n_sm >= 0 && (QS2 == 1 || QS2 == 2 || QS2 == 4);
+  if (by_rows) rows_pass(Nb, dred, kpad, G.t, G.part, QS2, gt, GT);
+  else flat_pass<8>(NTb, k, dpad, G.t, G.part, gt, GT);
   group_sync(g, GT);
   if (tr) trace_point(P, iter, 6);
 
   // Lambda-comp, residuals and exchange sums of the reduced rows
   float prim_f = 0.f, dual_f = 0.f;
   {
-    const int nrg = dpad >> 2;
-    const int QS = GT >= nrg ? small_div(GT, nrg) : 1;
+    const int QS = by_rows ? 1 : QS2;
     for (int red = gt; red < dred; red += GT) {
       float o = 0.f;
       for (int q = 0; q < QS; ++q) o += G.part[q * dpad + red];
@@ -965,7 +1017,7 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
       Rv[red] = rn;
       lhat[red] = lh;
       const int gi = reinterpret_cast<const int *>(rt + red * kRowRecord)[2];
-      Gnext[gi] = send(P, iter, it.sub, P.members[it.mem_off + small_div(red, rs_red)], gi, fmaf(-s, lh, rn));
+      Gnext[gi] = send(P, iter, it.sub, P.members + it.mem_off + small_div(red, rs_red), gi, fmaf(-s, lh, rn));
     }
   }
   // slot-0 rows: Psi fixed (e_c on the own member), lhat = alpha
@@ -989,7 +1041,7 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
     for (int c = 0; c < NX; ++c)
       if (aux == c) own = xj[c];
     const int gi = reinterpret_cast<const int *>(rt + p * kRowRecord)[2];
-    Gnext[gi] = send(P, iter, it.sub, P.members[it.mem_off + small_div(p - dred, NX)], gi, fmaf(-s, a, own));
+    Gnext[gi] = send(P, iter, it.sub, P.members + it.mem_off + small_div(p - dred, NX), gi, fmaf(-s, a, own));
   }
   finish_item<GT>(P, idx, it, extra, G, prim_f, dual_f, g, gt, lnc, iter);
 }
@@ -1271,7 +1323,7 @@ __global__ void __launch_bounds__(MAXT, 1) sweep_kernel(Params P) {
         const int idx = reinterpret_cast<const int *>(ex)[3];
         const bool tr = w0 == gi0 && wi == 0;
         if (compact && iter > 0)
-          project_compact<NX, GT>(P, idx, it, G.mtab + wi * P.max_nmem * MT, G.rtab + wi * P.max_dcol * kRowRecord,
+          project_compact<NX, GT, (MAXT <= 768)>(P, idx, it, G.mtab + wi * P.max_nmem * MT, G.rtab + wi * P.max_dcol * kRowRecord,
                                   ex, G, G.alpha + wi * P.max_dcol, arena,
                                   Gnext, g, gt, lnc, iter, iter == 1, tr);
         else

@@ -2,7 +2,7 @@
 profilers (ncu) and phase traces.
 
     python -m paper_2103_14990_gb300.profile_step --workload chain1024 \
-        --iters 50 --shape 1280701 --residency 2 --steps 3 [--trace] [--inner-qp coupled]
+        --iters 50 --shape 960701 --residency 2 --steps 3 [--trace] [--flush] [--inner-qp coupled]
 
 --shape is threads per group * 10000 + groups per CTA * 100 + wave (0 keeps
 the default plan); --iters runs exactly that many ADMM iterations per step
@@ -27,6 +27,7 @@ def main(argv=None) -> int:
     ap.add_argument("--compact", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--trace", action="store_true")
+    ap.add_argument("--flush", action="store_true", help="write 256 MiB before every step (L2 flushed, as in the benchmark)")
     ap.add_argument("--batch-count", type=int, default=256, help="instances of the mixed batch")
     ap.add_argument("--inner-qp", default="box", choices=["box", "block", "coupled"],
                     help="block: full SPD cost blocks; coupled: also 2 coupled state rows per slot")
@@ -66,7 +67,10 @@ def main(argv=None) -> int:
         info = s.info()
         print(json.dumps({"autotuned": {k: info[k] for k in ("group_threads", "groups_per_cta", "wave",
                                                               "resident_n_items", "iter_bytes_min")}}))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda") if a.flush else None
     for _ in range(a.steps):
+        if flush is not None:
+            flush.zero_()
         rc, st = s.step(x, u, xn, warm=pkg.WARM_COLD)
         ms = s.timing()[0]
         gbs = s.info()["iter_bytes_min"] * a.iters / (ms * 1e-3) / 1e9
