@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdlmpc.so")
 
-SOURCES = ["dlmpc_kernels.cu", "dlmpc_sweep.cu", "dlmpc_sweep_t768.cu", "dlmpc_learn.cu", "dlmpc_mlp.cu", "dlmpc_variants.cu",
+SOURCES = ["dlmpc_kernels.cu", "dlmpc_sweep.cu", "dlmpc_sweep_t768.cu", "dlmpc_sweep_t896.cu", "dlmpc_learn.cu", "dlmpc_mlp.cu", "dlmpc_variants.cu",
            "dlmpc_host.cpp", "dlmpc_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1,12 +1,14 @@
 // Persistent ADMM sweep (the kernel itself is in dlmpc_sweep.cuh): the
 // instantiations for CTAs of up to 1024 threads (64 registers per thread),
-// the dispatch to them or to the 768-thread tier (dlmpc_sweep_t768.cu, 80
-// registers per thread), and the host-side launch helpers.
+// the dispatch to them or to the 768- and 896-thread tiers
+// (dlmpc_sweep_t768.cu, 80 registers per thread; dlmpc_sweep_t896.cu, 72),
+// and the host-side launch helpers.
 #include "dlmpc_sweep.cuh"
 
 namespace dlmpc {
 
 const void *sweep_kernel_ptr_t768(int nx, int gt, bool blk);
+const void *sweep_kernel_ptr_t896(int nx, int gt, bool blk);
 
 template <int NX, int GT, bool BLK>
 static const void *sweep_fn() {
@@ -17,6 +19,7 @@ static const void *sweep_fn() {
 // `threads` (gt * groups per CTA) picks the register tier
 const void *sweep_kernel_ptr(int nx, int gt, bool blk, int threads) {
   if (threads <= 768) return sweep_kernel_ptr_t768(nx, gt, blk);
+  if (threads <= 896) return sweep_kernel_ptr_t896(nx, gt, blk);
 #define DLMPC_SWEEP_CASE(NXV)                                 \
   case NXV:                                                   \
     if (blk) {                                                \

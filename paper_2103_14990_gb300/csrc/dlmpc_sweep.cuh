@@ -882,9 +882,9 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
 // and the partials are added to zero in order q = 0, 1, ...; here partial q
 // takes the same terms in the same order (QS in {1, 2, 4} divides the four
 // entries of a 16-byte unit), and o[red] is that ordered sum.  The padded
-// entries of N and y are zeros and add exact zeros.  Used by the 80-register
-// tier only (ROWS): at 64 registers its live values would add spills to the
-// whole loop.
+// entries of N and y are zeros and add exact zeros.  Used by the 72- and
+// 80-register tiers only (ROWS): at 64 registers its live values would add
+// spills to the whole loop.
 __device__ __forceinline__ void rows_pass(const float *Nb, int dred, int kpad, const float *y, float *o_out, int QS,
                                           int gt, int GT) {
   for (int red = gt; red < dred; red += GT) {
@@ -1136,8 +1136,8 @@ __device__ __forceinline__ bool sweep_barrier(const Params &P, unsigned e, unsig
 // BLK: the Phi-step takes full cost blocks (phi_slots); a separate
 // instantiation keeps that solver out of the diagonal kernel's registers.
 // MAXT: the most threads a CTA of this instantiation may have, which sets its
-// register budget (65536 / MAXT per thread): 1024 gives 64 registers, 768
-// gives 80, enough for the loop to run without spills.
+// register budget (65536 / MAXT per thread): 1024 gives 64 registers, 896
+// gives 72 and 768 gives 80, enough for the loop to run without spills.
 template <int NX, int GT, bool BLK, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) sweep_kernel(Params P) {
   extern __shared__ __align__(16) float sm[];
@@ -1323,7 +1323,7 @@ __global__ void __launch_bounds__(MAXT, 1) sweep_kernel(Params P) {
         const int idx = reinterpret_cast<const int *>(ex)[3];
         const bool tr = w0 == gi0 && wi == 0;
         if (compact && iter > 0)
-          project_compact<NX, GT, (MAXT <= 768)>(P, idx, it, G.mtab + wi * P.max_nmem * MT, G.rtab + wi * P.max_dcol * kRowRecord,
+          project_compact<NX, GT, (MAXT <= 896)>(P, idx, it, G.mtab + wi * P.max_nmem * MT, G.rtab + wi * P.max_dcol * kRowRecord,
                                   ex, G, G.alpha + wi * P.max_dcol, arena,
                                   Gnext, g, gt, lnc, iter, iter == 1, tr);
         else
