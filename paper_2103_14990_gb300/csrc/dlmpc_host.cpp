@@ -27,7 +27,8 @@ cudaError_t launch_factor(const FactorParams &p, int grid, size_t smem, cudaStre
 cudaError_t launch_repack(const Item *scratch_items, const Item *items, int n_items, const float *src, float *dst,
                           cudaStream_t s);
 const void *sweep_kernel_ptr(int nx, int gt, bool blk, int threads);
-int sweep_group_floats(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad, int max_kpad, int max_nmem);
+int sweep_group_floats(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad, int max_kpad, int max_nmem,
+                       bool rows_cached);
 cudaStream_t mlp_stream(const dlmpc_mlp *mlp);
 cudaError_t launch_sweep(const Params &P, int gt, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_stats(const int32_t *inst_item_ptr, int n_inst, const float *item_r, const float *item_s,
@@ -143,6 +144,7 @@ struct dlmpc_ctx {
   int64_t n_floats = 0, q_floats = 0;
   // launch plan of the sweep kernel
   int grid = 0, gt = 128, ng = 4, wave = 2, grp_floats = 0, cta_floats = 0, max_local_inst = 1;
+  bool rows_cached = false;  // every group holds one wave: row records in shared memory
   size_t smem = 0;
   int64_t resident_n_items = 0, resident_state_items = 0;
   int residency = 2;  // 0: nothing resident, 1: compact iterate, Psi/Lambda and q resident, 2: also N
@@ -856,15 +858,21 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
   const int cta_floats = 8 + 4 * ((3 * max_li + 3) / 4);
   int64_t used_max = 0;
   std::vector<std::vector<std::vector<int32_t>>> groups(grid);
+  // groups of one wave keep their patch rows' records in shared memory
+  // (filled once per launch); otherwise the records are derived in the loop
+  bool rows_cached = true;
+  for (int b = 0; b < grid; ++b) {
+    groups[b] = lpt(ctx, ctas[b], ng);
+    for (auto &gl : groups[b]) rows_cached = rows_cached && (int)gl.size() <= wave;
+  }
   {  // N that is not resident is read from global memory directly
     const int grp = sweep_group_floats(nx, ctx->nu, gt, wave, ctx->max_dcol, ctx->max_dred_pad, ctx->max_kpad,
-                                       ctx->max_nmem);
+                                       ctx->max_nmem, rows_cached);
     const int64_t arena_cap = budget - (int64_t)ng * grp - cta_floats;
     if (arena_cap < 0) return ctx->fail(DLMPC_ERR_ARG, "shared-memory budget exceeded by the group buffers");
     used_max = 0;
     ctx->resident_n_items = ctx->resident_state_items = 0;
     for (int b = 0; b < grid; ++b) {
-      groups[b] = lpt(ctx, ctas[b], ng);
       int64_t used = 0;
       // resident Psi/Lambda and q first (round robin over groups)
       std::vector<int32_t> rr;
@@ -911,6 +919,7 @@ int plan_sweep(dlmpc_ctx *ctx, int gt, int ng, int wave, bool exact_groups = fal
         std::stable_partition(gl.begin(), gl.end(), [&](int id) { return ctx->items[id].n_sm >= 0; });
     }
     ctx->grp_floats = grp;
+    ctx->rows_cached = rows_cached;
   }
   ctx->grid = grid;
   ctx->gt = gt;
@@ -1496,6 +1505,7 @@ Params make_params(dlmpc_ctx *ctx, const float *x_dev, float *u_dev, float *xn_d
   P.grp_floats = ctx->grp_floats;
   P.cta_floats = ctx->cta_floats;
   P.max_local_inst = ctx->max_local_inst;
+  P.rows_cached = ctx->rows_cached ? 1 : 0;
   P.trace = ctx->trace ? ctx->d_trace.p : nullptr;
   P.skip_arrival_cta = ctx->skip_arrival_cta;
   P.compact = ctx->compact;

@@ -105,6 +105,7 @@ struct Params {
   int32_t grp_floats;         // floats per group region
   int32_t cta_floats;         // floats of the per-CTA counters (after the group regions)
   int32_t max_local_inst;
+  int32_t rows_cached;        // != 0: every group holds one wave; row records kept in shared memory
   unsigned long long *trace;  // optional [grid][kTraceIters][kTracePoints] globaltimer stamps
   int32_t skip_arrival_cta;   // test of the bounded waits: this CTA leaves before its first
                               // iteration barrier (-1 = none)

@@ -42,8 +42,9 @@ const void *sweep_kernel_ptr(int nx, int gt, bool blk, int threads) {
   return nullptr;
 }
 
-int sweep_group_floats(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad, int max_kpad, int max_nmem) {
-  return group_layout(nx, nu, gt, wave, max_dcol, max_dred_pad, max_kpad, max_nmem).total;
+int sweep_group_floats(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad, int max_kpad, int max_nmem,
+                       bool rows_cached) {
+  return group_layout(nx, nu, gt, wave, max_dcol, max_dred_pad, max_kpad, max_nmem, rows_cached).total;
 }
 
 cudaError_t launch_sweep(const Params &P, int gt, int grid, size_t smem, cudaStream_t s) {

@@ -51,32 +51,31 @@ constexpr int kItemFloats = (int)((sizeof(Item) + 3) / 4) + 4;
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
 __host__ __device__ inline int max3(int a, int b, int c) { return a > b ? (a > c ? a : c) : (b > c ? b : c); }
 
-// Floats of one row record (reduced order: the reduced rows of the patch,
-// then its slot-0 rows): int exchange read offset, int |Patch(m)|, int
-// exchange write offset, int aux; den = rho / (rho + 2 q s), lo, hi, 1/s.
-// aux: u index (sub * nu + b) of an own slot-0 input row, own state index c of
-// an own slot-0 state row, otherwise -1.
-constexpr int kRowRecord = 8;
-
 // Floats of one patch-member record: exchange read offset, |Patch|, 1/s (0
 // when s = 0), exchange write base, then x[nx], rho/(rho + 2 q s)[nx],
 // x_lo[nx], x_hi[nx], rho/(rho + 2 r s)[nu], u_lo[nu], u_hi[nu], 2 Q_m
 // [nx][nx], 2 R_m [nu][nu].
 __host__ __device__ inline int member_record(int nx, int nu) { return 4 + 4 * nx + 3 * nu + nx * nx + nu * nu; }
 
+// Floats of one cached row record (RowRec: four ints, four floats).
+constexpr int kRowRecord = 8;
+
 // Float offsets inside one group region; the host uses the same function.
+// rows_cached: the plan keeps one record per patch row (row_rec) in shared
+// memory, filled once per launch -- plans whose groups hold one wave of items;
+// other plans derive the records where they are used.
 __host__ __device__ inline GroupLayout group_layout(int nx, int nu, int gt, int wave, int max_dcol, int max_dred_pad,
-                                                    int max_kpad, int max_nmem) {
+                                                    int max_kpad, int max_nmem, bool rows_cached) {
   GroupLayout L;
   int o = 0;
   L.alpha = o;  o += round4(wave * max_dcol);
   L.vred = o;   o += nx * max_dred_pad;
-  L.psired = o; o += nx * max_dred_pad;
+  L.psired = L.vred;  // psi_red is written only after the last read of v_red
   L.t = o;      o += round4(nx * max_kpad);
   L.part = o;   o += round4(max3((gt / 32) * nx * max_kpad, 4 * gt, max_dred_pad));
   L.red = o;    o += round4(4 * (gt / 32));
   L.mtab = o;   o += round4(wave * max_nmem * member_record(nx, nu));
-  L.rtab = o;   o += wave * max_dcol * kRowRecord;
+  L.rtab = o;   o += rows_cached ? wave * max_dcol * kRowRecord : 0;
   L.icache = o; o += round4(wave * kItemFloats);
   L.mbar = o;   o += 4;
   L.total = o;
@@ -101,10 +100,59 @@ struct Group {
   unsigned phase;  // completed bulk copies on mbar
 };
 
-// Caches the wave's items (with their instance constants), fills the member
-// records of their patches and, from those, one record per patch row, so the
-// iteration loop reads nothing but the exchange sums (and non-resident N)
-// from global memory.
+// Record of row p of a patch (reduced order: the reduced rows, then the
+// slot-0 rows), from its member's record `tab`: exchange read offset,
+// |Patch(m)|, exchange write offset, aux (u index sub * nu + b of an own
+// slot-0 input row, own state index c of an own slot-0 state row, else -1);
+// den = rho / (rho + 2 q s), the row's bounds (slot-0 state rows unbounded),
+// 1/s (0 when s = 0).
+struct RowRec {
+  int rd, np, wr, aux;
+  float den, lo, hi, inv_s;
+};
+
+template <int NX>
+__device__ __forceinline__ RowRec row_rec(const Params &P, const Item &it, const float *tab, int p) {
+  const int MT = member_record(NX, P.nu);
+  const int rs_red = it.r_sub - NX, dred = it.dred, nxT = NX * it.T;
+  int mpos, r;
+  if (p < dred) {
+    mpos = small_div(p, rs_red);
+    r = p - mpos * rs_red + NX;
+  } else {
+    mpos = small_div(p - dred, NX);
+    r = p - dred - mpos * NX;
+  }
+  const float *rec = tab + mpos * MT;
+  const int *reci = reinterpret_cast<const int *>(rec);
+  const bool own = mpos == it.self_pos;
+  RowRec o;
+  o.aux = -1;
+  if (r < nxT) {
+    const int a = r % NX;
+    o.den = rec[4 + NX + a];
+    o.lo = r >= NX ? rec[4 + 2 * NX + a] : -INFINITY;
+    o.hi = r >= NX ? rec[4 + 3 * NX + a] : INFINITY;
+    if (own && r < NX) o.aux = r;
+  } else {
+    const int bb = (r - nxT) % P.nu;
+    o.den = rec[4 + 4 * NX + bb];
+    o.lo = rec[4 + 4 * NX + P.nu + bb];
+    o.hi = rec[4 + 4 * NX + 2 * P.nu + bb];
+    if (own && r < nxT + P.nu) o.aux = it.sub * P.nu + bb;
+  }
+  o.rd = reci[0] + r;
+  o.np = reci[1];
+  o.wr = reci[3] + r;
+  o.inv_s = rec[2];
+  return o;
+}
+
+// Caches the wave's items (with their instance constants) and fills the member
+// records of their patches, so the iteration loop reads nothing but the
+// exchange sums (and non-resident N) from global memory; with cached rows
+// (P.rows_cached) also the record of every patch row (row_rec), else each
+// row's record is derived from its member's where it is used.
 template <int NX>
 __device__ __forceinline__ void fill_wave(const Params &P, const int *items, int wn, float *icache, float *mtab,
                                           float *rtab, int g, int gt, int GT) {
@@ -152,49 +200,40 @@ __device__ __forceinline__ void fill_wave(const Params &P, const int *items, int
       for (int e2 = 0; e2 < P.nu * P.nu; ++e2) blk[NX * NX + e2] = P.rblk2[(int64_t)m * P.nu * P.nu + e2];
     }
   }
-  group_sync(g, GT);
+  if (!P.rows_cached) return;
+  group_sync(g, GT);  // the member records are complete
   for (int wi = 0; wi < wn; ++wi) {
     const Item &it = P.items[items[wi]];
     const float *tab = mtab + wi * P.max_nmem * MT;
     float *rt = rtab + wi * P.max_dcol * kRowRecord;
-    const int r_sub = it.r_sub, rs_red = r_sub - NX, dred = it.dred, nxT = NX * it.T;
-    for (int p = gt; p < r_sub * it.n_mem; p += GT) {
-      int mpos, r;
-      if (p < dred) {
-        mpos = p / rs_red;
-        r = p - mpos * rs_red + NX;
-      } else {
-        mpos = (p - dred) / NX;
-        r = p - dred - mpos * NX;
-      }
-      const float *rec = tab + mpos * MT;
-      const bool own = mpos == it.self_pos;
-      int aux = -1;
-      float den, lo, hi;
-      if (r < nxT) {
-        const int a = r % NX;
-        den = rec[4 + NX + a];
-        lo = r >= NX ? rec[4 + 2 * NX + a] : -INFINITY;
-        hi = r >= NX ? rec[4 + 3 * NX + a] : INFINITY;
-        if (own && r < NX) aux = r;
-      } else {
-        const int bb = (r - nxT) % P.nu;
-        den = rec[4 + 4 * NX + bb];
-        lo = rec[4 + 4 * NX + P.nu + bb];
-        hi = rec[4 + 4 * NX + 2 * P.nu + bb];
-        if (own && r < nxT + P.nu) aux = it.sub * P.nu + bb;
-      }
-      int *ri = reinterpret_cast<int *>(rt + p * kRowRecord);
-      ri[0] = reinterpret_cast<const int *>(rec)[0] + r;
-      ri[1] = reinterpret_cast<const int *>(rec)[1];
-      ri[2] = reinterpret_cast<const int *>(rec)[3] + r;
-      ri[3] = aux;
-      rt[p * kRowRecord + 4] = den;
-      rt[p * kRowRecord + 5] = lo;
-      rt[p * kRowRecord + 6] = hi;
-      rt[p * kRowRecord + 7] = rec[2];
+    for (int p = gt; p < it.r_sub * it.n_mem; p += GT) {
+      const RowRec r = row_rec<NX>(P, it, tab, p);
+      *reinterpret_cast<int4 *>(rt + p * kRowRecord) = make_int4(r.rd, r.np, r.wr, r.aux);
+      *reinterpret_cast<float4 *>(rt + p * kRowRecord + 4) = make_float4(r.den, r.lo, r.hi, r.inv_s);
     }
   }
+}
+
+// The cached record of row p.
+__device__ __forceinline__ RowRec cached_row(const float *rt, int p) {
+  const int4 a = *reinterpret_cast<const int4 *>(rt + p * kRowRecord);
+  const float4 c = *reinterpret_cast<const float4 *>(rt + p * kRowRecord + 4);
+  RowRec r;
+  r.rd = a.x;
+  r.np = a.y;
+  r.wr = a.z;
+  r.aux = a.w;
+  r.den = c.x;
+  r.lo = c.y;
+  r.hi = c.z;
+  r.inv_s = c.w;
+  return r;
+}
+
+// The record of row p: cached (rows_cached plans), else derived.
+template <int NX>
+__device__ __forceinline__ RowRec get_row(const Params &P, const Item &it, const float *tab, const float *rt, int p) {
+  return P.rows_cached ? cached_row(rt, p) : row_rec<NX>(P, it, tab, p);
 }
 
 __device__ __forceinline__ const Item &cached_item(const float *icache, int wi) {
@@ -203,6 +242,7 @@ __device__ __forceinline__ const Item &cached_item(const float *icache, int wi) 
 __device__ __forceinline__ const float *cached_extra(const float *icache, int wi) {
   return icache + wi * kItemFloats + (int)((sizeof(Item) + 3) / 4);
 }
+
 
 // Simulated lost messages (the fully distributed setting, Sec. V): output n
 // of SplitMix64 (Steele, Lea and Flood, 2014) seeded with `seed` ...
@@ -247,21 +287,23 @@ __device__ __forceinline__ void phi_row(const Params &P, int p, int dred, int au
 // (the reduced rows, then the slot-0 rows).  A thread takes two rows at a
 // time and issues the exchange loads of both before adding them.
 // W_ONLY: store w itself (the block Phi-step solves the slots afterwards).
-template <int GT, bool W_ONLY = false>
-__device__ __forceinline__ void phi_rows(const Params &P, const Item &it, const float *rt, const float *Gcur,
-                                         float *alpha_out, int gt) {
+template <int NX, int GT, bool W_ONLY, bool CACHED>
+__device__ __forceinline__ void phi_rows(const Params &P, const Item &it, const float *tab, const float *rt,
+                                         const float *Gcur, float *alpha_out, int gt) {
   const int r_sub = it.r_sub;
   const int dcol = r_sub * it.n_mem;
   for (int p = gt; p < dcol; p += 2 * GT) {
     const int p2 = p + GT;
     const bool two = p2 < dcol;
-    const int4 ia = *reinterpret_cast<const int4 *>(rt + p * kRowRecord);
-    const float4 ca = *reinterpret_cast<const float4 *>(rt + p * kRowRecord + 4);
+    const RowRec ra = CACHED ? cached_row(rt, p) : row_rec<NX>(P, it, tab, p);
+    const int4 ia = make_int4(ra.rd, ra.np, ra.wr, ra.aux);
+    const float4 ca = make_float4(ra.den, ra.lo, ra.hi, ra.inv_s);
     int4 ib = make_int4(0, 0, 0, -1);
     float4 cb = make_float4(0.f, 0.f, 0.f, 0.f);
     if (two) {
-      ib = *reinterpret_cast<const int4 *>(rt + p2 * kRowRecord);
-      cb = *reinterpret_cast<const float4 *>(rt + p2 * kRowRecord + 4);
+      const RowRec rb = CACHED ? cached_row(rt, p2) : row_rec<NX>(P, it, tab, p2);
+      ib = make_int4(rb.rd, rb.np, rb.wr, rb.aux);
+      cb = make_float4(rb.den, rb.lo, rb.hi, rb.inv_s);
     }
     const float *gp = Gcur + ia.x;
     const float *gp2 = Gcur + ib.x;
@@ -569,18 +611,20 @@ __device__ __forceinline__ void slot_explicit(const Params &P, int key, bool slo
 // One slot of the block Phi-step: its N rows start at reduced position p0 and
 // hold w (from the row pass) in alpha; the slot QP gives z, and alpha becomes
 // (z - w)/s per row (0 when s = 0); own slot-0 inputs also give u(tau).
-template <int N>
+template <int N, int NX>
 __device__ __forceinline__ void slot_solve(const Params &P, int key, bool slot0, int p0, int dred, const float *rec,
-                                           const float *C, const float *rt, float *alpha, float rho) {
+                                           const float *C, const Item &it, const float *tab, const float *rt,
+                                           float *alpha, float rho) {
   float w[N], lo[N], hi[N], z[N];
   int aux[N];
 #pragma unroll
   for (int a = 0; a < N; ++a) {
     const int p = p0 + a;
+    const RowRec rr = get_row<NX>(P, it, tab, rt, p);
     w[a] = alpha[p];
-    aux[a] = reinterpret_cast<const int *>(rt + p * kRowRecord)[3];
-    lo[a] = rt[p * kRowRecord + 5];
-    hi[a] = rt[p * kRowRecord + 6];
+    aux[a] = rr.aux;
+    lo[a] = rr.lo;
+    hi[a] = rr.hi;
     z[a] = w[a];
   }
   const float inv_s = rec[2];
@@ -627,15 +671,15 @@ __device__ void phi_slots(const Params &P, const Item &it, const float *tab, con
     const int key = P.expl ? 2 * P.members[it.mem_off + mpos] : 0;
     if (kk < T) {
       const int p0 = kk == 0 ? dred + mpos * NX : mpos * rs_red + (kk - 1) * NX;
-      slot_solve<NX>(P, key, kk == 0, p0, dred, rec, C, rt, alpha, rho);
+      slot_solve<NX, NX>(P, key, kk == 0, p0, dred, rec, C, it, tab, rt, alpha, rho);
     } else {
       const int p0 = mpos * rs_red + (T - 1) * NX + (kk - T) * nu;
       C += NX * NX;
       switch (nu) {
-        case 1: slot_solve<1>(P, key + 1, false, p0, dred, rec, C, rt, alpha, rho); break;
-        case 2: slot_solve<2>(P, key + 1, false, p0, dred, rec, C, rt, alpha, rho); break;
-        case 3: slot_solve<3>(P, key + 1, false, p0, dred, rec, C, rt, alpha, rho); break;
-        default: slot_solve<4>(P, key + 1, false, p0, dred, rec, C, rt, alpha, rho); break;
+        case 1: slot_solve<1, NX>(P, key + 1, false, p0, dred, rec, C, it, tab, rt, alpha, rho); break;
+        case 2: slot_solve<2, NX>(P, key + 1, false, p0, dred, rec, C, it, tab, rt, alpha, rho); break;
+        case 3: slot_solve<3, NX>(P, key + 1, false, p0, dred, rec, C, it, tab, rt, alpha, rho); break;
+        default: slot_solve<4, NX>(P, key + 1, false, p0, dred, rec, C, it, tab, rt, alpha, rho); break;
       }
     }
   }
@@ -1016,8 +1060,10 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
       const float rn = fmaf(s, o, Rv[red]);
       Rv[red] = rn;
       lhat[red] = lh;
-      const int gi = reinterpret_cast<const int *>(rt + red * kRowRecord)[2];
-      Gnext[gi] = send(P, iter, it.sub, P.members + it.mem_off + small_div(red, rs_red), gi, fmaf(-s, lh, rn));
+      const int mpos = small_div(red, rs_red);
+      const int gi = P.rows_cached ? reinterpret_cast<const int *>(rt + red * kRowRecord)[2]
+                                   : reinterpret_cast<const int *>(tab + mpos * MT)[3] + red - mpos * rs_red + NX;
+      Gnext[gi] = send(P, iter, it.sub, P.members + it.mem_off + mpos, gi, fmaf(-s, lh, rn));
     }
   }
   // slot-0 rows: Psi fixed (e_c on the own member), lhat = alpha
@@ -1035,12 +1081,13 @@ __device__ void project_compact(const Params &P, int idx, const Item &it, const 
       prim_f = fmaf(s * dp, dp, prim_f);
     }
     lhat[p] = a;
-    const int aux = reinterpret_cast<const int *>(rt + p * kRowRecord)[3];
+    const RowRec rr = get_row<NX>(P, it, tab, rt, p);
+    const int aux = rr.aux;
     float own = 0.f;
 #pragma unroll
     for (int c = 0; c < NX; ++c)
       if (aux == c) own = xj[c];
-    const int gi = reinterpret_cast<const int *>(rt + p * kRowRecord)[2];
+    const int gi = rr.wr;
     Gnext[gi] = send(P, iter, it.sub, P.members + it.mem_off + small_div(p - dred, NX), gi, fmaf(-s, a, own));
   }
   finish_item<GT>(P, idx, it, extra, G, prim_f, dual_f, g, gt, lnc, iter);
@@ -1144,7 +1191,8 @@ __global__ void __launch_bounds__(MAXT, 1) sweep_kernel(Params P) {
   const int tid = threadIdx.x;
   const int g = tid / GT, gt = tid - g * GT;
   const int b = blockIdx.x;
-  const GroupLayout L = group_layout(NX, P.nu, GT, P.wave, P.max_dcol, P.max_dred_pad, P.max_kpad, P.max_nmem);
+  const GroupLayout L =
+      group_layout(NX, P.nu, GT, P.wave, P.max_dcol, P.max_dred_pad, P.max_kpad, P.max_nmem, P.rows_cached != 0);
   float *gbase = sm + g * P.grp_floats;
   Group G;
   G.alpha = gbase + L.alpha;
@@ -1303,7 +1351,13 @@ __global__ void __launch_bounds__(MAXT, 1) sweep_kernel(Params P) {
       for (int wi = 0; wi < wn; ++wi) {
         const Item &it = cached_item(G.icache, wi);
         if (!lact[it.lslot]) continue;
-        phi_rows<GT, BLK>(P, it, G.rtab + wi * P.max_dcol * kRowRecord, Gcur, G.alpha + wi * P.max_dcol, gt);
+        // the record source is chosen once per patch, not per row
+        if (P.rows_cached)
+          phi_rows<NX, GT, BLK, true>(P, it, G.mtab + wi * P.max_nmem * MT, G.rtab + wi * P.max_dcol * kRowRecord,
+                                      Gcur, G.alpha + wi * P.max_dcol, gt);
+        else
+          phi_rows<NX, GT, BLK, false>(P, it, G.mtab + wi * P.max_nmem * MT, nullptr, Gcur, G.alpha + wi * P.max_dcol,
+                                       gt);
       }
       if constexpr (BLK) {
         group_sync(g, GT);  // every row's w is in alpha
@@ -1323,8 +1377,8 @@ __global__ void __launch_bounds__(MAXT, 1) sweep_kernel(Params P) {
         const int idx = reinterpret_cast<const int *>(ex)[3];
         const bool tr = w0 == gi0 && wi == 0;
         if (compact && iter > 0)
-          project_compact<NX, GT, (MAXT <= 896)>(P, idx, it, G.mtab + wi * P.max_nmem * MT, G.rtab + wi * P.max_dcol * kRowRecord,
-                                  ex, G, G.alpha + wi * P.max_dcol, arena,
+          project_compact<NX, GT, (MAXT <= 896)>(P, idx, it, G.mtab + wi * P.max_nmem * MT,
+                                  G.rtab + wi * P.max_dcol * kRowRecord, ex, G, G.alpha + wi * P.max_dcol, arena,
                                   Gnext, g, gt, lnc, iter, iter == 1, tr);
         else
           project_item<NX, GT>(P, idx, it, G.mtab + wi * P.max_nmem * MT, ex, G, G.alpha + wi * P.max_dcol, arena,
