@@ -255,6 +255,42 @@ def test_sweep_shapes_and_streaming(name, shape, torch):
     s.close()
 
 
+def test_row_records_cached_and_derived_agree_bit_for_bit(torch):
+    """A plan whose groups hold one wave of patches caches every row's record
+    in shared memory once per launch; a plan whose groups cycle through several
+    waves derives each record where it is used.  With the same threads per
+    group both give the same iterates bit for bit (fixed iterations and
+    closed-loop steps stopped by Conv), and the derived form matches the
+    oracle."""
+    import paper_2103_14990_gb300 as pkg
+    p = I.make_instance(400, 6, 2, seed=31, boxes=True, x0_dist="uniform")
+    runs = []
+    for shape, grid in ((1280301, 134), (1280101, 152)):  # 402 groups for 400 patches / about 3 per group
+        s = gpu_solver([p], torch)
+        s.set_option(pkg.OPT_SWEEP_SHAPE, shape)
+        assert s.info()["grid_ctas"] == grid
+        fixed = run_fixed(s, torch, p.x0, 30, export=False)
+        xa = torch.tensor(p.x0.astype(np.float32), device="cuda")
+        xb = torch.zeros_like(xa)
+        u = torch.zeros(p.n_sub, p.nu, device="cuda")
+        loop = []
+        for tau in range(3):
+            rc, st = s.step(xa, u, xb, warm=pkg.WARM_COLD if tau == 0 else pkg.WARM_CONVERGED)
+            loop.append((u.cpu().numpy().copy(), st[0]["iters"], st[0]["status"]))
+            xa, xb = xb, xa
+        runs.append((fixed, loop))
+        s.close()
+    (fa, la), (fb, lb) = runs
+    for k in (3, 4, 5, 6):
+        assert np.array_equal(fa[k], fb[k])
+    for (ua, ia, sa), (ub, ib, sb) in zip(la, lb):
+        assert ia == ib and sa == sb and np.array_equal(ua, ub)
+    o = O.Oracle(p)
+    ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=30)
+    assert rel(fb[3], ref.Psi) <= REL
+    assert max_patch_rel(o.lay, fb[3], ref.Psi) <= REL
+
+
 def test_graph_replay_is_bit_identical(torch):
     """Steps replayed from captured CUDA graphs (one graph per buffer set of a
     ping-pong closed loop) equal directly launched steps bit for bit."""
