@@ -216,8 +216,9 @@ def test_max_iter_status(torch):
     s.close()
 
 
+# threads per CTA span the three register tiers: <= 768, 769..896 (128 x 7), > 896 (64 x 15)
 SHAPES = [(128, 4, 2, 2), (128, 4, 1, 0), (64, 4, 3, 1), (256, 2, 2, 0), (128, 1, 1, 2), (64, 2, 4, 0),
-          (64, 15, 1, 1), (96, 5, 1, 2), (96, 3, 2, 0)]
+          (64, 15, 1, 1), (96, 5, 1, 2), (96, 3, 2, 0), (128, 7, 1, 2)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -392,6 +393,36 @@ def test_block_cost_fixed_iterations_parity(name, K, torch):
     assert rel(psi2, ref.Psi) <= REL
     assert rel(u2, u_ref) <= REL or np.max(np.abs(u2 - u_ref)) < 1e-7
     s.close()
+
+
+def test_block_cost_register_tiers_and_row_records_agree(torch):
+    """The block Phi-step in every register tier (CTAs of 1024, 896 and 512
+    threads at 128 threads per group), and with row records cached (one wave
+    per group) or derived (several waves per group), gives the same iterates
+    bit for bit; the 512-thread plan also against the oracle."""
+    import paper_2103_14990_gb300 as pkg
+    p = BLOCK["chain16_T10_d3_box_blk"]()
+    res = []
+    for shape in (1280801, 1280701, 1280401):
+        s = gpu_solver([p], torch)
+        s.set_option(pkg.OPT_SWEEP_SHAPE, shape)
+        assert s.info()["threads_per_cta"] == (shape // 10000) * ((shape // 100) % 100)
+        res.append(run_fixed(s, torch, p.x0, 25, export=False))
+        s.close()
+    for r in res[1:]:
+        assert np.array_equal(r[3], res[0][3]) and np.array_equal(r[4], res[0][4]) and np.array_equal(r[5], res[0][5])
+    o = O.Oracle(p)
+    ref = O.admm(o.lay, o.blocks, p.x0, fixed_iters=25)
+    assert rel(res[2][3], ref.Psi) <= REL
+    q = I.with_block_costs(I.make_instance(400, 6, 2, seed=35, boxes=True, x0_dist="uniform"), seed=36)
+    out = []
+    for shape, grid in ((1280301, 134), (1280101, 152)):  # one patch per group / about 3 per group
+        s = gpu_solver([q], torch)
+        s.set_option(pkg.OPT_SWEEP_SHAPE, shape)
+        assert s.info()["grid_ctas"] == grid
+        out.append(run_fixed(s, torch, q.x0, 20, export=False))
+        s.close()
+    assert np.array_equal(out[0][3], out[1][3]) and np.array_equal(out[0][5], out[1][5])
 
 
 def test_block_cost_stopped_closed_loop(torch):
