@@ -95,7 +95,7 @@ __device__ __forceinline__ void group_sync(int g, int gt_threads) {
 
 struct Group {
   float *alpha, *vred, *psired, *t, *part, *mtab, *rtab, *icache;
-  double *red;
+  float *red;
   uint64_t *mbar;
   unsigned phase;  // completed bulk copies on mbar
 };
@@ -737,10 +737,13 @@ __device__ __forceinline__ void apply_n(const float *Nb, const float *tv, const 
 
 // Conv of one patch from the per-thread squared residual partials (Sec. II-A
 // stopping rule, per subsystem): ||Phi - Psi||_F <= eps_p and
-// rho ||Psi - Psi_prev||_F <= eps_d.  GB300 runs FP64 at a small fraction of
-// FP32: sums of a few squares stay in FP32 (tree order, relative error
-// ~1e-6), the per-warp sums are combined in FP64 and squared residuals are
-// compared (no square root on the path).
+// rho ||Psi - Psi_prev||_F <= eps_d.  The sums of squares are FP32 (per
+// thread, then tree order over the warp and over the group's warps: relative
+// error ~1e-6) and squared residuals are compared (no square root on the
+// path).  GB300 runs FP64 at a small fraction of the FP32 rate, and the
+// dependent FP64 chain this combine used to be (conversions, shuffles, adds,
+// products on every patch of every iteration) sat on the iteration's critical
+// path while adding nothing to a threshold test on FP32 partials.
 template <int GT>
 __device__ __forceinline__ void finish_item(const Params &P, int idx, const Item &it, const float *extra, Group &G,
                                             float prim_f, float dual_f, int g, int gt, unsigned *lnc, int iter) {
@@ -748,25 +751,25 @@ __device__ __forceinline__ void finish_item(const Params &P, int idx, const Item
   const float prim_w = warp_sum_f(prim_f);
   const float dual_w = warp_sum_f(dual_f);
   if ((gt & 31) == 0) {
-    G.red[2 * (gt >> 5)] = (double)prim_w;
-    G.red[2 * (gt >> 5) + 1] = (double)dual_w;
+    G.red[2 * (gt >> 5)] = prim_w;
+    G.red[2 * (gt >> 5) + 1] = dual_w;
   }
   group_sync(g, GT);
   if (gt < 32) {
-    // lane w < kWarps holds warp w's sums; FP64 tree over the lanes
+    // lane w < kWarps holds warp w's sums; tree over the lanes
     constexpr int kTree = kWarps <= 1 ? 1 : kWarps <= 2 ? 2 : kWarps <= 4 ? 4 : 8;  // power of two >= kWarps
-    double pp = gt < kWarps ? G.red[2 * gt] : 0.0;
-    double dd = gt < kWarps ? G.red[2 * gt + 1] : 0.0;
+    float pp = gt < kWarps ? G.red[2 * gt] : 0.f;
+    float dd = gt < kWarps ? G.red[2 * gt + 1] : 0.f;
 #pragma unroll
     for (int o = kTree / 2; o > 0; o >>= 1) {
       pp += __shfl_xor_sync(0xffffffffu, pp, o);
       dd += __shfl_xor_sync(0xffffffffu, dd, o);
     }
     if (gt != 0) return;
-    const double rho = extra[0], epsp = extra[1], epsd = extra[2];
+    const float rho = extra[0], epsp = extra[1], epsd = extra[2];
     const bool conv = pp <= epsp * epsp && rho * rho * dd <= epsd * epsd;
-    const float rj = sqrtf((float)pp);
-    const float sj = (float)rho * sqrtf((float)dd);
+    const float rj = sqrtf(pp);
+    const float sj = rho * sqrtf(dd);
     P.item_r[idx] = rj;
     P.item_s[idx] = sj;
     if (!(isfinite(rj) && isfinite(sj))) set_error(P.err, DLMPC_ERR_NONFINITE, blockIdx.x, iter, it.sub);
@@ -889,7 +892,7 @@ __device__ void project_item(const Params &P, int idx, const Item &it, const flo
   if (tr) trace_point(P, iter, 6);
 
   // slot-0 states pinned to e_c; Lambda-comp; residuals; new exchange sums
-  float prim_f = 0.f, dual_f = 0.f;  // FP32 partials per thread and warp, combined in FP64
+  float prim_f = 0.f, dual_f = 0.f;  // FP32 partials per thread, then per warp and per group
   for (int f = gt, mpos = mpos0, r = r0; f < dcol; f += GT, mpos += dm, r += dr) {
     if (r >= r_sub) { r -= r_sub; ++mpos; }
     const int red = mpos * rs_red + r - NX;
@@ -1200,7 +1203,7 @@ __global__ void __launch_bounds__(MAXT, 1) sweep_kernel(Params P) {
   G.psired = gbase + L.psired;
   G.t = gbase + L.t;
   G.part = gbase + L.part;
-  G.red = reinterpret_cast<double *>(gbase + L.red);
+  G.red = gbase + L.red;
   G.mtab = gbase + L.mtab;
   G.rtab = gbase + L.rtab;
   G.icache = gbase + L.icache;
