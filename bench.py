@@ -44,28 +44,28 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_sweep.c
 # launch ran, and the on-chip figures of the same kernel.  A workload without
 # a capture of the current source reports null.
 NCU = {
-    "src_sha256": "942373359638267f9d08e924ee7e6fa2a1189336fb72832e4138d37fcac8cd50",
+    "src_sha256": "8f22efc932aa50a386e7dd4463c5a3cdc40606edbc33faab2232bbc35d4c05f7",
     "workloads": {
         # one bench-plan launch (7 groups of 96, 80-register tier) of 200
         # fixed iterations after an L2 flush: the operators come from DRAM
         # once per launch, the loop is served by shared memory and L2 (full
         # capture of 50 iterations, same plan)
-        "chain1024": {"dram_bytes_per_launch": 63612160 + 704000, "iters_per_launch": 200,
-                      "onchip": {"dram_throughput_pct": 1.32, "lts_throughput_pct": 18.36,
-                                 "l2_hit_rate_pct": 92.73, "issue_active_pct": 39.8, "warps_active_pct": 32.8}},
-        # 20 fixed iterations of the bench's plan (15 groups of 64, 64-register
-        # tier): N and N^T streamed from DRAM every iteration
-        "grid64": {"dram_bytes_per_launch": 13418498304 + 214538496, "iters_per_launch": 20,
-                   "onchip": {"dram_throughput_pct": 44.8, "lts_throughput_pct": 28.7,
-                              "l2_hit_rate_pct": 22.2, "issue_active_pct": 18.6, "warps_active_pct": 46.9}},
+        "chain1024": {"dram_bytes_per_launch": 63608832 + 792832, "iters_per_launch": 200,
+                      "onchip": {"dram_throughput_pct": 1.40, "lts_throughput_pct": 19.55,
+                                 "l2_hit_rate_pct": 92.68, "issue_active_pct": 41.8, "warps_active_pct": 32.8}},
+        # 20 fixed iterations of the bench's plan (10 groups of 96, wave 2,
+        # 64-register tier): N and N^T streamed from DRAM every iteration
+        "grid64": {"dram_bytes_per_launch": 13037459456 + 213839872, "iters_per_launch": 20,
+                   "onchip": {"dram_throughput_pct": 44.0, "lts_throughput_pct": 28.2,
+                              "l2_hit_rate_pct": 23.0, "issue_active_pct": 19.4, "warps_active_pct": 46.9}},
         # 64 of the 256 instances (a few GB on the device), 10 fixed
         # iterations of the bench's plan (8 groups of 128, 64-register tier);
         # scaled to the 256-instance launch by the algorithmic bytes (DRAM /
         # algorithmic = 1.89 on the 64-instance capture)
         "batch256": {"dram_bytes_per_launch": int(1.887 * 9889012444 * 20), "iters_per_launch": 20,
-                     "scaled_from": "64-instance capture: 49090359552 B per 10 iterations, 2.60 GB algorithmic each",
-                     "onchip": {"dram_throughput_pct": 38.3, "lts_throughput_pct": 24.6,
-                                "l2_hit_rate_pct": 22.4, "issue_active_pct": 13.9, "warps_active_pct": 50.0}},
+                     "scaled_from": "64-instance capture: 49087535104 B per 10 iterations, 2.60 GB algorithmic each",
+                     "onchip": {"dram_throughput_pct": 39.2, "lts_throughput_pct": 25.2,
+                                "l2_hit_rate_pct": 22.4, "issue_active_pct": 14.2, "warps_active_pct": 50.2}},
     },
 }
 
