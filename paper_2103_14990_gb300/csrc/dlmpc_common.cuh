@@ -114,6 +114,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsign
 // fast division, so the float result floors exactly (no integer division).
 __device__ __forceinline__ int small_div(int a, int b) { return (int)__fdividef((float)a + 0.5f, (float)b); }
 
+// The last `left` (< V) rows of a thread in one predicated chunk of V: the
+// rows past `left` add exact zeros, so the sums equal any chunking's.
+template <int V>
+__device__ __forceinline__ void flat_tail(const float *mp, const float *vp, int step, int QS, int left, float4 &acc) {
+  float4 m4[V];
+  float vv[V];
+#pragma unroll
+  for (int u = 0; u < V; ++u) {
+    m4[u] = u < left ? *reinterpret_cast<const float4 *>(mp + u * step) : make_float4(0.f, 0.f, 0.f, 0.f);
+    vv[u] = u < left ? vp[u * QS] : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < V; ++u) {
+    acc.x = fmaf(m4[u].x, vv[u], acc.x);
+    acc.y = fmaf(m4[u].y, vv[u], acc.y);
+    acc.z = fmaf(m4[u].z, vv[u], acc.z);
+    acc.w = fmaf(m4[u].w, vv[u], acc.w);
+  }
+}
+
 template <int U>
 __device__ __forceinline__ void flat_pass(const float *M, int rows, int ld, const float *vec, float *part, int gt,
                                           int GT) {
@@ -127,7 +147,7 @@ __device__ __forceinline__ void flat_pass(const float *M, int rows, int ld, cons
     int left = rows > q ? small_div(rows - q + QS - 1, QS) : 0;  // rows of this thread
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     // whole chunks of U rows without predicates (running pointers), then
-    // one predicated tail chunk
+    // one predicated tail chunk of U or U/2 rows
     for (; left >= U; left -= U) {
       float4 m4[U];
       float vv[U];
@@ -146,22 +166,8 @@ __device__ __forceinline__ void flat_pass(const float *M, int rows, int ld, cons
       mp += U * step;
       vp += U * QS;
     }
-    if (left > 0) {
-      float4 m4[U];
-      float vv[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        m4[u] = u < left ? *reinterpret_cast<const float4 *>(mp + u * step) : make_float4(0.f, 0.f, 0.f, 0.f);
-        vv[u] = u < left ? vp[u * QS] : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        acc.x = fmaf(m4[u].x, vv[u], acc.x);
-        acc.y = fmaf(m4[u].y, vv[u], acc.y);
-        acc.z = fmaf(m4[u].z, vv[u], acc.z);
-        acc.w = fmaf(m4[u].w, vv[u], acc.w);
-      }
-    }
+    if (left > U / 2) flat_tail<U>(mp, vp, step, QS, left, acc);
+    else if (left > 0) flat_tail<U / 2>(mp, vp, step, QS, left, acc);
     *reinterpret_cast<float4 *>(part + q * ld + 4 * cg) = acc;
   }
 }

@@ -1149,10 +1149,10 @@ __device__ __forceinline__ void red_add_release_u64(unsigned long long *p, unsig
 // Returns false on timeout or when any CTA has recorded an error; `total` is
 // the number of not-converged patches summed over the grid.
 __device__ __forceinline__ bool sweep_barrier(const Params &P, unsigned e, unsigned my_nc, unsigned long long *prev_hi,
-                                              unsigned &total, int iter) {
+                                              unsigned &total, int iter, bool synced = false) {
   __shared__ int ok_sh;
   __shared__ unsigned total_sh;
-  __syncthreads();
+  if (!synced) __syncthreads();  // the CTA's writes before the arrival (the caller may have synchronised)
   if (threadIdx.x == 0) {
     unsigned long long *ctr = P.bar + (e % 3);
     red_add_release_u64(ctr, 1ull | ((unsigned long long)my_nc << 32));
@@ -1405,7 +1405,7 @@ __global__ void __launch_bounds__(MAXT, 1) sweep_kernel(Params P) {
         if (multi && lnc[t]) atomicAdd(P.notconv + slot * P.n_inst + P.cta_inst[li0 + t], lnc[t]);
       }
     }
-    ok = sweep_barrier(P, e_bar++, my_nc, prev_hi, total, iter);
+    ok = sweep_barrier(P, e_bar++, my_nc, prev_hi, total, iter, true);
     if (!ok) break;
     trace_point(P, iter, 5);
     if (b == 0) {
