@@ -37,35 +37,36 @@ sys.path.insert(0, ROOT)
 METRIC = "MPC steps/s & ADMM iters/s, batched+warm-start vs plain at 1e-4 rel; HBM GB/s"
 UNIT = "MPC steps/s"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SRC = os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", "dlmpc_sweep.cuh")
+# the sweep kernel's source: its template and the device helpers it inlines
+KERNEL_SRC = [os.path.join(ROOT, "paper_2103_14990_gb300", "csrc", f) for f in ("dlmpc_sweep.cuh", "dlmpc_common.cuh")]
 # Counters of one sweep_kernel launch per workload from ncu captures of the
 # kernel source whose sha256 is given (the capture commands are recorded with
 # the profile summaries): DRAM bytes read + written, the iterations that
 # launch ran, and the on-chip figures of the same kernel.  A workload without
 # a capture of the current source reports null.
 NCU = {
-    "src_sha256": "8f22efc932aa50a386e7dd4463c5a3cdc40606edbc33faab2232bbc35d4c05f7",
+    "src_sha256": "3f742c50df985204ab7d47e1c040b0602b1ea05ab514b9a5c4d87eb0c043c5b3",
     "workloads": {
         # one bench-plan launch (7 groups of 96, 80-register tier) of 200
         # fixed iterations after an L2 flush: the operators come from DRAM
         # once per launch, the loop is served by shared memory and L2 (full
         # capture of 50 iterations, same plan)
-        "chain1024": {"dram_bytes_per_launch": 63608832 + 792832, "iters_per_launch": 200,
-                      "onchip": {"dram_throughput_pct": 1.40, "lts_throughput_pct": 19.55,
-                                 "l2_hit_rate_pct": 92.68, "issue_active_pct": 41.8, "warps_active_pct": 32.8}},
-        # 20 fixed iterations of the bench's plan (10 groups of 96, wave 2,
-        # 64-register tier): N and N^T streamed from DRAM every iteration
-        "grid64": {"dram_bytes_per_launch": 13037459456 + 213839872, "iters_per_launch": 20,
-                   "onchip": {"dram_throughput_pct": 44.0, "lts_throughput_pct": 28.2,
-                              "l2_hit_rate_pct": 23.0, "issue_active_pct": 19.4, "warps_active_pct": 46.9}},
+        "chain1024": {"dram_bytes_per_launch": 63611136 + 765952, "iters_per_launch": 200,
+                      "onchip": {"dram_throughput_pct": 1.43, "lts_throughput_pct": 19.86,
+                                 "l2_hit_rate_pct": 92.66, "issue_active_pct": 41.3, "warps_active_pct": 32.8}},
+        # 20 fixed iterations of the bench's plan (15 groups of 64, 64-register
+        # tier): N and N^T streamed from DRAM every iteration
+        "grid64": {"dram_bytes_per_launch": 13411877632 + 214867712, "iters_per_launch": 20,
+                   "onchip": {"dram_throughput_pct": 45.3, "lts_throughput_pct": 29.0,
+                              "l2_hit_rate_pct": 22.3, "issue_active_pct": 18.7, "warps_active_pct": 46.9}},
         # 64 of the 256 instances (a few GB on the device), 10 fixed
         # iterations of the bench's plan (8 groups of 128, 64-register tier);
         # scaled to the 256-instance launch by the algorithmic bytes (DRAM /
         # algorithmic = 1.89 on the 64-instance capture)
-        "batch256": {"dram_bytes_per_launch": int(1.887 * 9889012444 * 20), "iters_per_launch": 20,
-                     "scaled_from": "64-instance capture: 49087535104 B per 10 iterations, 2.60 GB algorithmic each",
-                     "onchip": {"dram_throughput_pct": 39.2, "lts_throughput_pct": 25.2,
-                                "l2_hit_rate_pct": 22.4, "issue_active_pct": 14.2, "warps_active_pct": 50.2}},
+        "batch256": {"dram_bytes_per_launch": int(1.888 * 9889012444 * 20), "iters_per_launch": 20,
+                     "scaled_from": "64-instance capture: 49100904960 B per 10 iterations, 2.60 GB algorithmic each",
+                     "onchip": {"dram_throughput_pct": 39.2, "lts_throughput_pct": 25.1,
+                                "l2_hit_rate_pct": 22.3, "issue_active_pct": 14.0, "warps_active_pct": 49.9}},
     },
 }
 
@@ -96,7 +97,11 @@ def bench_config(prob, world: int, inner_qp: str = "box", stale_prob: float = 0.
 
 
 def kernel_sha() -> str:
-    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    """sha256 of the kernel source files, concatenated in order."""
+    h = hashlib.sha256()
+    for path in KERNEL_SRC:
+        h.update(open(path, "rb").read())
+    return h.hexdigest()
 
 
 def ncu_record(workload_name: str, inner_qp: str, stale_prob: float) -> dict:
