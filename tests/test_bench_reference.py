@@ -40,3 +40,44 @@ def test_all_cores_baseline_aggregates_processes():
     assert out["oracle_admm_iters_per_s"] > 0
     # four steps of ten iterations at the aggregate rate (plus the u/dynamics tail)
     assert out["value"] <= 4 / (40 / out["oracle_admm_iters_per_s"]) + 1e-9
+
+
+def test_ncu_record_is_gated_by_the_kernel_source(tmp_path, monkeypatch):
+    """`traffic` and the on-chip counters are reported only while the kernel
+    source hashes to the captured one (the template and the device helpers
+    it inlines); any edit of either file, another inner QP or lost messages
+    turn them into nulls."""
+    import bench
+    monkeypatch.setattr(bench, "kernel_sha", lambda: bench.NCU["src_sha256"])  # as if captured on this source
+    rec = bench.ncu_record("chain1024", "box", 0.0)
+    w = bench.NCU["workloads"]["chain1024"]
+    assert rec["traffic"] == w["dram_bytes_per_launch"] and rec["traffic_launch_iters"] == w["iters_per_launch"]
+    assert bench.ncu_record("batch256", "box", 0.0)["traffic_scaled_from"]
+    assert bench.ncu_record("chain1024", "block", 0.0) == {"traffic": None, "onchip": None}
+    assert bench.ncu_record("chain1024", "box", 0.1) == {"traffic": None, "onchip": None}
+    assert bench.ncu_record("chain10", "box", 0.0) == {"traffic": None, "onchip": None}
+    edited = []
+    for i, path in enumerate(bench.KERNEL_SRC):
+        f = tmp_path / f"src{i}"
+        f.write_bytes(open(path, "rb").read() + (b"// edited\n" if i == 1 else b""))
+        edited.append(str(f))
+    monkeypatch.undo()
+    sha = bench.kernel_sha()
+    monkeypatch.setattr(bench, "KERNEL_SRC", edited)
+    assert bench.kernel_sha() != sha
+    assert bench.ncu_record("chain1024", "box", 0.0) == {"traffic": None, "onchip": None}
+
+
+def test_roofline_counts_algorithmic_bytes_over_kernel_time():
+    """achieved = algorithmic bytes per iteration x iterations of the launches
+    (the longest instance of each) / summed sweep-kernel event time; frac
+    against the given peak."""
+    import bench
+    info = {"iter_bytes_min": 46_532_272, "iter_bytes": 82_839_712}
+    rec = {"iters": [[1000], [1000], [58]], "kms": [10.0, 10.0, 0.58]}
+    r = bench.alg_roofline(info, rec, 6651.7, "measured")
+    expect = 46_532_272 * 2058 / (20.58e-3) / 1e9
+    assert abs(r["achieved"] - round(expect, 1)) < 1e-6
+    assert r["frac"] == round(expect / 6651.7, 4) and r["bound"] == "hbm"
+    assert r["mean_launch_ms"] == round(20.58 / 3, 4)
+    assert r["algorithmic_bytes_per_iter"] == 46_532_272 and r["kernel_load_bytes_per_iter"] == 82_839_712
