@@ -1,4 +1,4 @@
-"""Spatial sharding of one network over two ranks (gloo, CPU): the
+"""Spatial sharding of one network over two to four ranks (gloo, CPU): the
 partitioner, the halo index maps and the exchange of the row sums, and the
 all-reduce of the Conv counts, against the single-process FP64 oracle.
 
@@ -100,9 +100,8 @@ def _worker(rank, world, port, kind, out):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("kind", ["chain", "grid"])
-def test_two_rank_sharded_admm_matches_the_oracle(kind):
-    world = 2
+@pytest.mark.parametrize("kind,world", [("chain", 2), ("grid", 2), ("chain", 3), ("grid", 4)])
+def test_sharded_admm_matches_the_oracle(kind, world):
     ctx = mp.get_context("spawn")
     with ctx.Manager() as m:
         out = m.dict()
